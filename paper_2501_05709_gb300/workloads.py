@@ -1,0 +1,442 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module only *generates* inputs: element node coordinates and face
+connectivity of structured hexahedral/quadrilateral meshes, closed-form
+initial and reference flow fields evaluated at caller-supplied coordinates,
+seeded perturbations, and FW-H data-surface point sets.  It holds none of the
+Flux Reconstruction arithmetic (no solution/flux points, no operators, no
+metrics, no fluxes), so the oracle and the CUDA library each derive those on
+their own from the same mesh description.
+
+Mesh description (the layout ``fr_mesh_load`` takes):
+
+* ``nodes``: float64 ``[E][(q+1)**dim][dim]`` with q the geometry order
+  (1: bi/trilinear, 2: bi/triquadratic).  Nodes sit at the equispaced
+  reference points {-1, (0,) 1} of each direction, local node index
+  ``a + (q+1)*b (+ (q+1)**2 * c)`` with ``a`` along xi_1 (fastest).
+* ``conn``: int32 ``[E][2*dim][3]``.  Face ``2*d`` is xi_d = -1, face
+  ``2*d+1`` is xi_d = +1.  An interior face holds ``(neighbour element,
+  neighbour face, orientation)``; a boundary face holds ``(-tag, 0, 0)`` with
+  tag ``BC_WALL`` (no-slip adiabatic wall) or ``BC_FARFIELD``
+  (characteristic far field).  Every generator here emits orientation 0
+  (face points correspond one to one in the same order).
+
+Workload recipes (paper Section 3.1 and Appendix C shapes):
+
+* ``box_mesh``: uniform periodic box, optionally curved by a smooth periodic
+  displacement and/or with walls on the y faces.
+* ``ogrid_mesh``: spanwise-periodic O-grid of quadratic hexahedra around a
+  NACA 4-digit section (Section 3.4 parametrisation) or a circle, straight
+  radial rays to a circular far field, geometric radial stretching.
+* ``isentropic_vortex``, ``taylor_green``: closed-form flow fields.
+* ``perturbed_uniform``: free stream plus a seeded uniform velocity
+  perturbation per solution point (PCG64).
+* ``cylinder_surface`` / ``sphere_surface``: FW-H data surfaces (Section 3.1
+  spacing 0.01c with the 0.005c offset from the periodic planes; Appendix C
+  sphere with 30 polar rings and azimuthal spacing 2*pi/45).
+* ``monopole_field`` / ``dipole_field``: Appendix C closed-form acoustic
+  fields in a uniformly moving medium.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+BC_WALL = 1
+BC_FARFIELD = 2
+
+GAMMA = 1.4
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+
+def _elem_nodes_from_grid(grid, q, dim, ne, shift=None):
+    """Cut a structured node grid into per-element node blocks.
+
+    grid: [n_0, .., n_{dim-1}, dim] node coordinates, q*ne[d] (+1 when not
+    periodic) nodes along direction d.  A node index that wraps past the end
+    of a periodic direction d takes the node at the wrapped index plus the
+    period vector shift[d] (zero for a closed curve such as an O-grid ring).
+    """
+    shape = grid.shape[:dim]
+    if shift is None:
+        shift = np.zeros((dim, dim))
+    shift = np.asarray(shift, float)
+    loc = np.stack(np.meshgrid(*[np.arange(q + 1)] * dim, indexing="ij"), axis=-1)
+    loc = loc.reshape(-1, dim)
+    # local node index a + (q+1) b (+ (q+1)^2 c): a fastest
+    order = np.lexsort(tuple(loc[:, d] for d in range(dim)))
+    loc = loc[order]
+    eidx = np.stack(np.meshgrid(*[np.arange(n) for n in ne], indexing="ij"), axis=-1)
+    eidx = eidx.reshape(-1, dim)
+    eorder = np.lexsort(tuple(eidx[:, d] for d in range(dim)))
+    eidx = eidx[eorder]                                   # element e: e_0 fastest
+    gi = q * eidx[:, None, :] + loc[None, :, :]          # [E, nloc, dim]
+    wrap = gi // np.asarray(shape)
+    gi = gi % np.asarray(shape)
+    out = grid[tuple(gi[..., d] for d in range(dim))]
+    out = out + np.einsum("end,dc->enc", wrap.astype(float), shift)
+    return np.ascontiguousarray(out)
+
+
+def _structured_conn(ne, periodic, bc_lo, bc_hi):
+    """Face connectivity of a structured block of ne[0] x ne[1] (x ne[2]) elements.
+
+    periodic[d]: wrap direction d.  bc_lo[d]/bc_hi[d]: boundary tag used on the
+    xi_d = -1 / +1 block faces when direction d is not periodic.
+    """
+    dim = len(ne)
+    E = int(np.prod(ne))
+    conn = np.zeros((E, 2 * dim, 3), dtype=np.int32)
+    strides = [1, ne[0], ne[0] * (ne[1] if dim > 1 else 1)]
+    for e in range(E):
+        idx = []
+        r = e
+        for d in range(dim):
+            idx.append(r % ne[d])
+            r //= ne[d]
+        for d in range(dim):
+            for side in (0, 1):
+                f = 2 * d + side
+                j = idx[d] + (1 if side else -1)
+                if 0 <= j < ne[d] or periodic[d]:
+                    j %= ne[d]
+                    nb = e + (j - idx[d]) * strides[d]
+                    conn[e, f] = (nb, 2 * d + (1 - side), 0)
+                else:
+                    tag = bc_hi[d] if side else bc_lo[d]
+                    conn[e, f] = (-tag, 0, 0)
+    return conn
+
+
+def box_mesh(dim, n, lo, hi, q=1, periodic=None, walls_y=False, curve=0.0, seed=0):
+    """Uniform box of n^dim (or n[0] x n[1] x n[2]) elements.
+
+    curve > 0 displaces every node by a smooth field periodic on the box
+    (amplitude ``curve`` times the element size, seeded phases), which makes
+    elements curved (q=2) or skewed (q=1) while periodic faces still match.
+    walls_y puts BC_WALL on both y faces (direction 1 not periodic).
+    """
+    ne = list(n) if np.ndim(n) else [int(n)] * dim
+    lo = np.broadcast_to(np.asarray(lo, float), (dim,)).copy()
+    hi = np.broadcast_to(np.asarray(hi, float), (dim,)).copy()
+    if periodic is None:
+        periodic = [True] * dim
+    periodic = list(periodic)
+    if walls_y:
+        periodic[1] = False
+    npts = [q * ne[d] + (0 if periodic[d] else 1) for d in range(dim)]
+    axes = [lo[d] + (hi[d] - lo[d]) * np.arange(npts[d]) / (q * ne[d]) for d in range(dim)]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1)
+    if curve > 0.0:
+        rng = np.random.default_rng(seed)
+        L = hi - lo
+        h = np.min(L / np.asarray(ne))
+        ph = rng.uniform(0, 2 * np.pi, size=(dim, dim))
+        disp = np.zeros_like(grid)
+        for c in range(dim):
+            arg = np.zeros(grid.shape[:-1])
+            for d in range(dim):
+                arg = arg + 2 * np.pi * (grid[..., d] - lo[d]) / L[d] + ph[c, d]
+            amp = curve * h
+            field = amp * np.sin(arg)
+            # keep wall planes flat so wall faces stay at y = lo/hi
+            if walls_y:
+                yy = (grid[..., 1] - lo[1]) / L[1]
+                field = field * np.sin(np.pi * yy)
+            disp[..., c] = field
+        grid = grid + disp
+    shift = np.diag(hi - lo)
+    nodes = _elem_nodes_from_grid(grid, q, dim, ne, shift)
+    bc = [BC_WALL] * dim
+    conn = _structured_conn(ne, periodic, bc, bc)
+    return nodes, conn
+
+
+def naca4_surface(m, pc, t, beta):
+    """NACA 4-digit section point at curve parameter beta in [0, 2*pi).
+
+    Chord from x=0 (leading edge) to x=1 (trailing edge), closed trailing
+    edge.  beta runs clockwise from the trailing edge: lower surface for
+    beta in [0, pi], upper surface for beta in [pi, 2*pi].
+    """
+    beta = np.asarray(beta, float)
+    x = 0.5 * (1.0 + np.cos(beta))
+    yt = 5.0 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2
+                    + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+    if m > 0.0:
+        fore = x < pc
+        yc = np.where(fore, m / pc ** 2 * (2 * pc * x - x ** 2),
+                      m / (1 - pc) ** 2 * ((1 - 2 * pc) + 2 * pc * x - x ** 2))
+        dyc = np.where(fore, 2 * m / pc ** 2 * (pc - x), 2 * m / (1 - pc) ** 2 * (pc - x))
+    else:
+        yc = np.zeros_like(x)
+        dyc = np.zeros_like(x)
+    th = np.arctan(dyc)
+    upper = np.sin(beta) < 0.0  # beta in (pi, 2pi)
+    sgn = np.where(upper, 1.0, -1.0)
+    xs = x - sgn * yt * np.sin(th)
+    ys = yc + sgn * yt * np.cos(th)
+    return xs, ys
+
+
+def ogrid_mesh(n_theta, n_r, n_z, span, r_outer=10.0, first_cell=2e-3, body="naca",
+               naca=(0.02, 0.4, 0.12), radius=0.5, center=(0.5, 0.0), q=2):
+    """Spanwise-periodic O-grid of (q=2) quadratic hexahedra around a body.
+
+    Element e = i_theta + n_theta*(i_r + n_r*i_z).  xi_1 runs clockwise around
+    the body (periodic), xi_2 radially outward (face 2 = BC_WALL on the body,
+    face 3 = BC_FARFIELD at r_outer), xi_3 along the span (periodic).
+    body="naca" uses the NACA 4-digit (m, p, t) section, body="circle" a
+    circle of the given radius about ``center``.
+    """
+    nt = q * n_theta
+    beta = 2 * np.pi * np.arange(nt) / nt
+    cx, cy = center
+    if body == "naca":
+        xs, ys = naca4_surface(*naca, beta)
+    else:
+        xs = cx + radius * np.cos(-beta)
+        ys = cy + radius * np.sin(-beta)
+    xo = cx + r_outer * np.cos(-beta)
+    yo = cy + r_outer * np.sin(-beta)
+    # geometric stretching: first element height ~ first_cell relative to r_outer
+    D = r_outer
+    target = first_cell / D
+
+    def frac(ratio):
+        return (ratio - 1.0) / (ratio ** n_r - 1.0)
+
+    lo_r, hi_r = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo_r + hi_r)
+        if frac(mid) > target:
+            lo_r = mid
+        else:
+            hi_r = mid
+    ratio = 0.5 * (lo_r + hi_r)
+    jr = np.arange(q * n_r + 1) / q
+    s = (ratio ** jr - 1.0) / (ratio ** n_r - 1.0)
+    zz = span * np.arange(q * n_z) / (q * n_z)
+    grid = np.empty((nt, q * n_r + 1, q * n_z, 3))
+    for k, z in enumerate(zz):
+        grid[:, :, k, 0] = (1 - s[None, :]) * xs[:, None] + s[None, :] * xo[:, None]
+        grid[:, :, k, 1] = (1 - s[None, :]) * ys[:, None] + s[None, :] * yo[:, None]
+        grid[:, :, k, 2] = z
+    shift = np.zeros((3, 3))
+    shift[2, 2] = span
+    nodes = _elem_nodes_from_grid(grid, q, 3, [n_theta, n_r, n_z], shift)
+    conn = _structured_conn([n_theta, n_r, n_z], [True, False, True],
+                            [0, BC_WALL, 0], [0, BC_FARFIELD, 0])
+    return nodes, conn
+
+
+# --------------------------------------------------------------------------
+# closed-form flow fields (conserved variables [rho, rho*V, rho*E])
+# --------------------------------------------------------------------------
+
+def primitive_to_conserved(rho, vel, p, gamma=GAMMA):
+    vel = np.asarray(vel)
+    ke = 0.5 * rho * np.sum(vel * vel, axis=0)
+    return np.concatenate([rho[None], rho[None] * vel, (p / (gamma - 1.0) + ke)[None]], axis=0)
+
+
+def isentropic_vortex(x, t=0.0, beta=5.0, mach=0.5, gamma=GAMMA, period=10.0, center=(0.0, 0.0)):
+    """2D isentropic vortex advected at U = mach*sqrt(gamma) along +x.
+
+    rho_inf = p_inf = T_inf = 1.  x: [..., 2] coordinates.  The displacement
+    from the advected centre is wrapped into the periodic box [-5, 5)^2.
+    Returns conserved variables with shape [4, ...].
+    """
+    U = mach * math.sqrt(gamma)
+    dx = x[..., 0] - (center[0] + U * t)
+    dy = x[..., 1] - center[1]
+    dx = (dx + 0.5 * period) % period - 0.5 * period
+    dy = (dy + 0.5 * period) % period - 0.5 * period
+    r2 = dx * dx + dy * dy
+    f = np.exp(0.5 * (1.0 - r2))
+    du = -beta / (2 * np.pi) * dy * f
+    dv = beta / (2 * np.pi) * dx * f
+    T = 1.0 - (gamma - 1.0) * beta ** 2 / (8.0 * gamma * np.pi ** 2) * np.exp(1.0 - r2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    return primitive_to_conserved(rho, np.stack([U + du, dv]), p, gamma)
+
+
+def taylor_green(x, mach=0.1, gamma=GAMMA):
+    """3D Taylor-Green vortex on [0, 2*pi]^3 (unit velocity, isothermal rho = p/p0)."""
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = np.zeros_like(u)
+    p0 = 1.0 / (gamma * mach ** 2)
+    p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+    rho = p / p0
+    return primitive_to_conserved(rho, np.stack([u, v, w]), p, gamma)
+
+
+def freestream(mach, aoa_deg, dim=3, gamma=GAMMA):
+    """Free-stream state: rho=1, |V|=1 at angle aoa in the x-y plane, p=1/(gamma M^2)."""
+    a = math.radians(aoa_deg)
+    vel = [math.cos(a), math.sin(a)] + ([0.0] if dim == 3 else [])
+    return 1.0, np.array(vel), 1.0 / (gamma * mach ** 2)
+
+
+def uniform_state(shape, rho, vel, p, gamma=GAMMA):
+    """Conserved state [nvar, *shape] of a uniform flow."""
+    vel = np.asarray(vel, float)
+    r = np.full(shape, rho)
+    V = np.stack([np.full(shape, v) for v in vel])
+    P = np.full(shape, p)
+    return primitive_to_conserved(r, V, P, gamma)
+
+
+def perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.01, seed=0, gamma=GAMMA):
+    """Uniform flow plus U(-a, a)*|V| added to every velocity component at every
+    solution point (PCG64 with the given seed).  Returns float64 [E][nvar][nsp].
+    """
+    vel = np.asarray(vel, float)
+    dim = vel.size
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dV = rng.uniform(-amplitude, amplitude, size=(dim, E, nsp)) * np.linalg.norm(vel)
+    V = vel[:, None, None] + dV
+    r = np.full((E, nsp), rho)
+    P = np.full((E, nsp), p)
+    u = primitive_to_conserved(r, V, P, gamma)  # [nvar, E, nsp]
+    return np.ascontiguousarray(np.moveaxis(u, 0, 1))
+
+
+def random_smooth_state(x, seed=0, gamma=GAMMA, amp=0.1, periods=None):
+    """A smooth positive state from a few seeded Fourier modes of x ([..., dim])."""
+    rng = np.random.default_rng(seed)
+    dim = x.shape[-1]
+    if periods is None:
+        periods = np.ones(dim)
+    periods = np.asarray(periods, float)
+
+    def mode():
+        k = rng.integers(1, 3, size=dim)
+        ph = rng.uniform(0, 2 * np.pi)
+        arg = sum(2 * np.pi * k[d] * x[..., d] / periods[d] for d in range(dim)) + ph
+        return np.sin(arg)
+
+    rho = 1.0 + amp * mode()
+    vel = np.stack([0.3 + amp * mode() for _ in range(dim)])
+    p = 1.0 + amp * mode()
+    return primitive_to_conserved(rho, vel, p, gamma)
+
+
+# --------------------------------------------------------------------------
+# FW-H data surfaces
+# --------------------------------------------------------------------------
+
+def cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=0.2):
+    """Closed cylindrical permeable surface about the spanwise axis.
+
+    Panel centres every ``spacing`` in arc length and in z, the first and last
+    spanwise rows spacing/2 from the periodic planes.  Returns (y [N,3],
+    outward unit normal [N,3], panel area [N]).
+    """
+    n_az = int(round(2 * np.pi * radius / spacing))
+    n_z = int(round(span / spacing))
+    ang = 2 * np.pi * (np.arange(n_az) + 0.5) / n_az
+    z = spacing * (np.arange(n_z) + 0.5) * (span / (n_z * spacing))
+    A, Z = np.meshgrid(ang, z, indexing="xy")
+    A = A.ravel()
+    Z = Z.ravel()
+    y = np.stack([center[0] + radius * np.cos(A), center[1] + radius * np.sin(A), Z], axis=1)
+    nrm = np.stack([np.cos(A), np.sin(A), np.zeros_like(A)], axis=1)
+    area = np.full(A.shape, (2 * np.pi * radius / n_az) * (span / n_z))
+    return y, nrm, area
+
+
+def sphere_surface(radius=1.0, n_polar=30, dphi=2 * np.pi / 45):
+    """Sphere split into n_polar rings; ring i at theta_i=(i+1/2)pi/n_polar with
+    max(1, round(2*pi*sin(theta_i)/dphi)) panels of equal area (exact band area
+    divided evenly).  Returns (y [N,3], outward unit normal [N,3], area [N]).
+    """
+    ys, ns, As = [], [], []
+    for i in range(n_polar):
+        tlo = i * np.pi / n_polar
+        thi = (i + 1) * np.pi / n_polar
+        th = 0.5 * (tlo + thi)
+        nphi = max(1, int(round(2 * np.pi * np.sin(th) / dphi)))
+        band = 2 * np.pi * radius ** 2 * (np.cos(tlo) - np.cos(thi))
+        phi = 2 * np.pi * (np.arange(nphi) + 0.5) / nphi
+        n = np.stack([np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi),
+                      np.full(nphi, np.cos(th))], axis=1)
+        ys.append(radius * n)
+        ns.append(n)
+        As.append(np.full(nphi, band / nphi))
+    return np.concatenate(ys), np.concatenate(ns), np.concatenate(As)
+
+
+# --------------------------------------------------------------------------
+# Appendix C closed-form acoustic fields in a uniformly moving medium
+# --------------------------------------------------------------------------
+
+def _moving_medium_radii(r, M):
+    """Amplitude radius R*, phase radius R and their x-gradients for r = x - y_s."""
+    M = np.asarray(M, float)
+    b2 = 1.0 / (1.0 - M @ M)
+    Mr = r @ M
+    rr = np.sum(r * r, axis=-1)
+    Rs = np.sqrt(rr + b2 * Mr ** 2) / np.sqrt(b2)
+    R = b2 * (Rs - Mr)
+    dRs = (r + b2 * Mr[..., None] * M) / (b2 * Rs[..., None])
+    dR = b2 * (dRs - M)
+    return Rs, R, dRs, dR
+
+
+def monopole_field(x, t, M, A=1.0, omega=10 * np.pi, c0=340.75, rho0=1.234, gamma=GAMMA):
+    """Monopole of Appendix C.1 at the origin, medium moving at Mach vector M.
+
+    phi = A/(4 pi R*) exp(i omega (t - R/c0)); u' = grad phi; p' = -rho0 (d/dt +
+    c0 M.grad) phi; rho' = p'/c0^2 (real parts).  x: [..., 3], t: scalar or
+    broadcastable.  Returns dict with rho, vel (total, [...,3]), p, and p'.
+    """
+    M = np.asarray(M, float)
+    Rs, R, dRs, dR = _moving_medium_radii(x, M)
+    ph = np.exp(1j * omega * (t - R / c0))
+    phi = A / (4 * np.pi * Rs) * ph
+    gphi = (A / (4 * np.pi)) * ph[..., None] * (-dRs / Rs[..., None] ** 2
+                                               - 1j * omega / c0 * dR / Rs[..., None])
+    return _acoustic_out(phi, gphi, M, omega, c0, rho0, gamma)
+
+
+def dipole_field(x, t, M, A=1.0, omega=10 * np.pi, c0=340.75, rho0=1.234, gamma=GAMMA, h=1e-4):
+    """Dipole of Appendix C.2: phi_d = d(phi_m)/d x_2, axis along x_2.
+
+    The x_2 derivative and the gradient of phi_d are taken by 4th-order
+    central differences of the closed-form monopole potential with step h.
+    """
+    M = np.asarray(M, float)
+
+    def phim(xx):
+        Rs, R, _, _ = _moving_medium_radii(xx, M)
+        return A / (4 * np.pi * Rs) * np.exp(1j * omega * (t - R / c0))
+
+    def d(f, xx, k):
+        e = np.zeros(3)
+        e[k] = h
+        return (-f(xx + 2 * e) + 8 * f(xx + e) - 8 * f(xx - e) + f(xx - 2 * e)) / (12 * h)
+
+    def phid(xx):
+        return d(phim, xx, 1)
+
+    phi = phid(x)
+    gphi = np.stack([d(phid, x, k) for k in range(3)], axis=-1)
+    return _acoustic_out(phi, gphi, M, omega, c0, rho0, gamma)
+
+
+def _acoustic_out(phi, gphi, M, omega, c0, rho0, gamma):
+    p0 = rho0 * c0 ** 2 / gamma
+    pp = -rho0 * (1j * omega * phi + c0 * (gphi @ M))
+    up = np.real(gphi)
+    pr = np.real(pp)
+    U = c0 * M
+    return {"rho": rho0 + pr / c0 ** 2, "vel": U + up, "p": p0 + pr, "pprime": pr,
+            "p0": p0, "rho0": rho0}
