@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Throughput of the FR/LES hot path on one GB300 per rank.
+
+A step is one classic RK4 step (four FR residual evaluations of the
+compressible Navier-Stokes equations with Rusanov and BR2 fluxes, fused with
+the stage updates) of the 3D Taylor-Green vortex at Re = 1600, M = 0.1 on a
+periodic 32^3 hexahedral box at FR order p = 3 (2,097,152 solution points per
+variable).  The metric is DOF x RK-stages per second (DOF = solution points,
+counted once).  Inputs are synthetic and seeded; the mesh is generated.
+
+The timed region replays a CUDA graph of one step K times on one stream with
+the state resident in HBM; the working set (~0.27 GB in FP32) is larger than
+the 129 MB L2.  `value` is the FP32 path; the FP64 path on the same workload
+is reported beside it, with the FP32 state deviation from FP64 after the
+timed steps.  `--gpus N` under torchrun runs N independent replicas (the path
+does not need a collective); value = all replicas' work / max time.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the only other place this script runs it) and prints its line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*RK-stages/s per GB300 (mixed/batched vs FP64 plain at stated error), %roofline"
+UNIT = "DOF*RK-stages/s"
+GAMMA = 1.4
+MACH = 0.1
+DT = 2.5e-4
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def oracle_sample(n=4, min_seconds=10.0, max_steps=50):
+    """FP64 numpy oracle: RK4 steps of the same TGV workload on an n^3 box,
+    one BLAS thread; returns (DOF*stages/s, steps, seconds, dof)."""
+    import numpy as np
+
+    from oracle.fr import FRSolver
+    from oracle.mesh import Mesh
+    from oracle.physics import NavierStokes
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = W.box_mesh(3, n, 0.0, 2 * math.pi, q=1)
+    m = Mesh(nodes, conn, 3)
+    s = FRSolver(m, NavierStokes(3, mu=1.0 / 1600.0))
+    u = np.ascontiguousarray(np.moveaxis(W.taylor_green(m.xsp, mach=MACH), 0, 1))
+    u = s.rk4_step(u, DT)  # warm-up
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps and (time.perf_counter() - t0 < min_seconds or k == 0):
+        u = s.rk4_step(u, DT)
+        k += 1
+    dt = time.perf_counter() - t0
+    dof = m.E * m.Nsp
+    return dof * 4 * k / dt, k, dt, dof
+
+
+def run_oracle_subprocess(min_seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(min_seconds=%f)))" % (ROOT, min_seconds))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    v, k, dt, dof = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"TGV p=3 on a 4^3-element box ({dof} DOF), {k} RK4 steps in {dt:.1f} s, numpy FP64, 1 BLAS thread"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = str(gpu_index)
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", self.idx, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" == r[5 + i].strip()})
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def algorithmic_bytes(E, p, rsz, viscous=True, dim=3):
+    """Minimum HBM bytes per RK stage of each kernel (affine mesh): every array
+    the kernel must touch, read or written once."""
+    np_ = p + 1
+    nsp, nfp, nf, nv = np_ ** dim, np_ ** (dim - 1), 2 * dim, dim + 2
+    u = nv * nsp * rsz
+    tr = nf * nv * nfp * rsz
+    geo = (dim * dim + 1 + nf * dim) * rsz + nf * 4
+    traces = E * (u + tr)
+    visc = E * (u + tr + tr + geo) if viscous else 0
+    rk = (2 + 4 + 4 + 3) / 4.0 * u
+    resid = E * (u + tr + (2 * tr if viscous else 0) + geo + rk)
+    return {"traces": traces, "visc": visc, "resid": resid}
+
+
+def gpu_leg(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2501_05709_gb300 import build as B
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    n, p = 32, 3
+    nodes, conn = W.box_mesh(3, n, 0.0, 2 * math.pi, q=1)
+    p_inf = 1.0 / (GAMMA * MACH ** 2)
+
+    def opts(prec):
+        return F.options(order=p, precision=prec, viscous=True, mu=1.0 / 1600.0, p_inf=p_inf, dt=DT)
+
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = F.fr_mesh_load((nodes, conn), opts(F.FR_FP32))
+    xsp = F.fr_sp_coords(ctx)
+    u0 = np.ascontiguousarray(np.moveaxis(W.taylor_green(xsp, mach=MACH), 0, 1))
+    E, nsp = ctx.nelem, ctx.nsp
+    dof = E * nsp
+    F.fr_state_set(ctx, u0)
+    tile = F.fr_autotune(ctx)
+    F.fr_state_set(ctx, u0)
+    F.fr_rk_step_graph(ctx, args.warmup, sh)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world > 1:
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    clocks = Clocks(local_rank) if rank == 0 else None
+    time.sleep(0.3)
+    n0 = F.fr_launch_count(ctx)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    F.fr_rk_step_graph(ctx, args.steps, sh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    launches = F.fr_launch_count(ctx) - n0
+    ck = clocks.stop() if clocks else None
+    value = world * dof * 4 * args.steps / (ms / 1e3)
+
+    # per-kernel durations of the same steps, events around each launch
+    kms, kn = F.fr_profile_step(ctx, args.steps, sh)
+    hbm, peak_kind = peaks()
+    ab = algorithmic_bytes(E, p, 4)
+    resid_ms = kms[2] / max(kn[2], 1)
+    achieved = ab["resid"] / (resid_ms / 1e3) / 1e9
+    kernels = {
+        "traces": {"avg_ms": kms[0] / max(kn[0], 1), "launches": int(kn[0]),
+                   "gbs": ab["traces"] / (kms[0] / max(kn[0], 1) / 1e3) / 1e9},
+        "visc_face": {"avg_ms": kms[1] / max(kn[1], 1), "launches": int(kn[1]),
+                      "gbs": ab["visc"] / (kms[1] / max(kn[1], 1) / 1e3) / 1e9},
+        "residual_rk": {"avg_ms": resid_ms, "launches": int(kn[2]), "gbs": achieved},
+    }
+    u32 = F.fr_state_get(ctx)
+    steps_done = args.warmup + 2 * args.steps
+
+    # end to end through the C-ABI: pinned host state in, step, KE integral out
+    host = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
+    host.numpy()[...] = u0
+    hnp = host.numpy()
+    F.fr_state_set(ctx, hnp, stream=sh)
+    F.fr_rk_step_graph(ctx, 1, sh)
+    F.fr_integrals(ctx)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F.fr_state_set(ctx, hnp, stream=sh)
+        F.fr_rk_step_graph(ctx, 1, sh)
+        F.fr_integrals(ctx)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * dof * 4 * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(8 * 6 * min(1024, (dof + 255) // 256))}
+    ctx.close()
+
+    # FP64 path, same workload, same number of steps
+    fp64 = None
+    if not args.no_fp64:
+        c64 = F.fr_mesh_load((nodes, conn), opts(F.FR_FP64))
+        F.fr_state_set(c64, u0)
+        F.fr_autotune(c64)
+        F.fr_state_set(c64, u0)
+        F.fr_rk_step_graph(c64, args.warmup, sh)
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        F.fr_rk_step_graph(c64, args.steps, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms64 = max_over_ranks(a.elapsed_time(b))
+        F.fr_rk_step_graph(c64, args.steps, sh)  # same step count as the FP32 state
+        u64 = F.fr_state_get(c64)
+        dev = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
+        ke = F.fr_integrals(c64)[-1]
+        c64.close()
+        fp64 = {"value": world * dof * 4 * args.steps / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / args.steps,
+                "fp32_state_rel_l2_vs_fp64": dev, "steps_compared": steps_done, "ke_fp64": ke}
+    return {
+        "value": value, "ms": ms, "launches": launches, "clocks": ck, "kernels": kernels, "tile_epb": tile,
+        "roofline": {"bound": "hbm", "kernel": "k_residual (FR residual + RK4 stage)", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_launch": ab["resid"]},
+        "e2e": e2e, "fp64": fp64, "dof": dof, "elements": E,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": "tgv32_p3", "description": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, "
+              "FR p=3 (2,097,152 DOF), Rusanov+BR2, RK4 dt=2.5e-4", "elements": 32768, "order": 3,
+              "dof_per_variable": 2097152, "step": "one RK4 step = 4 residual stages",
+              "l2": "working set larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = run_oracle_subprocess(min_seconds=max(3.0, 1.0 * args.steps))
+        line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    r = gpu_leg(args, rank, world, local_rank)
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline:
+            try:
+                cb = run_oracle_subprocess(min_seconds=10.0)
+            except Exception as e:  # reported, not fatal
+                cb = {"value": None, "error": str(e)[-300:]}
+        config["autotuned_elements_per_block"] = r["tile_epb"]
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
+                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * libfr -- GB300 (sm_103a) Flux Reconstruction LES residual, RK4 update,
+ * wall forces, FW-H data-surface sampling and FW-H integration.
+ *
+ * The operations follow Hamedi & Vermeire, "Far-Field Aeroacoustic Shape
+ * Optimization Using Large Eddy Simulation" (arXiv 2501.05709):
+ *   - compressible Navier-Stokes in conservation form, Section 2.1, Eqs. 1-7;
+ *   - Flux Reconstruction on curved hexahedra with implicit LES, Section 1,
+ *     Section 2.1, Section 3.1;
+ *   - mean lift/drag, Section 3.2 (Table 1) and Eq. 8;
+ *   - data-surface sampling of rho, p, velocity, Section 3.1 and 3.4;
+ *   - FW-H moving-medium integration with spanwise duplication, Appendix B
+ *     (Eqs. B.1-B.14) and Section 3.3.1.
+ * FR details the paper leaves open are fixed as: Gauss-Legendre solution and
+ * flux points, DG or Huynh-g2 correction functions, Rusanov inviscid flux,
+ * BR2 viscous flux, classic four-stage RK4.
+ *
+ * Conventions for every call:
+ *   - return value: FR_OK (0) or a negative FR_E* code; fr_last_error()
+ *     gives a message for the calling thread.
+ *   - host arrays passed in are read during the call and never retained;
+ *   - device pointers passed in belong to the caller, are used in stream
+ *     order on the given cudaStream_t (passed as void*; NULL = legacy default
+ *     stream) and are never freed by the library;
+ *   - the library owns its internal device buffers (freed by fr_destroy);
+ *   - there is no CPU fallback: every compute call runs CUDA kernels and
+ *     fails with FR_ECUDA when no usable GPU is present.
+ *
+ * Canonical state layout: [E][nvar][Nsp], E elements (all candidates
+ * concatenated in load order), nvar = dim + 2 conserved variables
+ * (rho, rho*V_1..V_dim, rho*E), Nsp = (p+1)^dim solution points with index
+ * i_0 + (p+1) i_1 (+ (p+1)^2 i_2), i_0 along xi_1 fastest.
+ */
+#ifndef LIBFR_FR_H
+#define LIBFR_FR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_OK 0
+#define FR_EINVAL -1     /* bad argument */
+#define FR_ENOMEM -2     /* device or host allocation failed */
+#define FR_ECUDA -3      /* CUDA runtime error (no device, launch failure) */
+#define FR_ENONFINITE -4 /* NaN or Inf found in the state */
+#define FR_ETIMEOUT -5   /* a bounded device wait expired */
+#define FR_EWINDOW -6    /* FW-H: the unified observer window is empty */
+#define FR_EMESH -7      /* invalid geometry or connectivity */
+
+#define FR_FP64 0        /* all state and arithmetic in double */
+#define FR_FP32 1        /* state and arithmetic in float; metrics computed in
+                            double and rounded once; force, energy and FW-H
+                            accumulators in double */
+
+#define FR_CORR_DG 0       /* g_L = right Radau polynomial of degree p+1 */
+#define FR_CORR_HUYNH_G2 1 /* Huynh's g2 */
+
+#define FR_BC_WALL 1      /* no-slip adiabatic wall (slip wall when inviscid) */
+#define FR_BC_FARFIELD 2  /* characteristic (Riemann-invariant) far field */
+
+typedef struct fr_ctx fr_ctx;
+
+/* One mesh (one candidate).  nodes: [nelem][(q+1)^dim][dim] double, nodes at
+ * the equispaced reference points of each direction, local index
+ * a + (q+1) b (+ (q+1)^2 c).  conn: [nelem][2 dim][3] int32; face 2d is
+ * xi_d = -1, face 2d+1 is xi_d = +1; an interior face holds (neighbour
+ * element, neighbour face, orientation) with the orientation code of the face
+ * point map (dim 2: bit 0 reverses; dim 3: bit 2 swaps the two face indices,
+ * then bit 0 / bit 1 reverse the first / second); a boundary face holds
+ * (-FR_BC_WALL or -FR_BC_FARFIELD, 0, 0).  Element numbers are local to the
+ * candidate. */
+typedef struct {
+    int dim;
+    int nelem;
+    int geom_order;
+    const double* nodes;
+    const int32_t* conn;
+} fr_mesh_desc;
+
+typedef struct {
+    int order;          /* p, 1..4 */
+    int correction;     /* FR_CORR_* */
+    int precision;      /* FR_FP64 or FR_FP32 */
+    int viscous;        /* 0: Euler, 1: Navier-Stokes (BR2) */
+    double gamma;       /* ratio of specific heats (1.4 in Section 2.1) */
+    double prandtl;     /* Pr (0.71 in Section 2.1) */
+    double mu;          /* constant dynamic viscosity */
+    double br2_eta;     /* BR2 lifting penalty (1.0 default) */
+    double rho_inf;     /* free stream: far-field state, force scale, */
+    double p_inf;       /*   sampled-deviation reference               */
+    double vel_inf[3];
+    double dt;          /* RK4 time step */
+    double lift_dir[3]; /* unit vectors for C_L / C_D */
+    double drag_dir[3];
+    double ref_area;    /* chord * span; C = F / (1/2 rho_inf |V_inf|^2 ref_area) */
+} fr_options;
+
+/* Context sizes: out[0]=dim, [1]=order p, [2]=nvar, [3]=Nsp, [4]=total
+ * elements E, [5]=ncand, [6]=precision, [7]=1 if every element is affine. */
+int fr_ctx_dims(const fr_ctx* ctx, int64_t out[8]);
+
+/* fr_mesh_load (Section 3.1 mesh of curved hexahedra; FR set-up of Section 1):
+ * builds reference operators, curved-element metric terms in
+ * conservative-curl form, shared face normals and the face-pair table for
+ * ncand meshes (m[0..ncand-1]) concatenated into one batch, uploads them and
+ * allocates the state.  Errors: FR_EINVAL (bad sizes or options), FR_EMESH
+ * (non-positive Jacobian, asymmetric or mismatched connectivity), FR_ENOMEM,
+ * FR_ECUDA.  *out is set to NULL on error. */
+int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* o, fr_ctx** out);
+
+/* Releases every device and host resource of ctx (NULL is accepted). */
+int fr_destroy(fr_ctx* ctx);
+
+/* Message of the last error raised on this thread ("" if none). */
+const char* fr_last_error(void);
+
+/* Physical solution-point coordinates, host double [E][Nsp][dim], for cand
+ * (or all candidates when cand < 0).  The caller owns xyz. */
+int fr_sp_coords(const fr_ctx* ctx, int cand, double* xyz);
+
+/* Element offset and count of candidate cand within the batch. */
+int fr_cand_range(const fr_ctx* ctx, int cand, int64_t* first, int64_t* count);
+
+/* State upload / download in the canonical layout as double.  cand < 0
+ * addresses the whole batch.  on_device != 0: u is a device pointer.
+ * fr_state_set also resets the RK stage buffers.  The call synchronises the
+ * given stream before returning. */
+int fr_state_set(fr_ctx* ctx, int cand, const double* u, int on_device, void* stream);
+int fr_state_get(fr_ctx* ctx, int cand, double* u, int on_device, void* stream);
+
+/* fr_residual (Eq. 1 semi-discretised: du/dt = R(u)): one residual evaluation
+ * of the whole batch.  u and R are device pointers in the context precision
+ * (double for FR_FP64, float for FR_FP32), canonical layout, E*nvar*Nsp
+ * values each; they must not overlap.  Uses the context's trace buffers, so
+ * calls on one context must not run concurrently. */
+int fr_residual(fr_ctx* ctx, const void* u, void* R, void* stream);
+
+/* fr_rk_step: advances the internal state by nsteps classic RK4 steps of
+ * size dt (each step: 4 residual evaluations fused with the stage update),
+ * accumulating the wall force every step and appending one record to every
+ * registered FW-H surface every step.  Enqueued on stream; returns without
+ * synchronising. */
+int fr_rk_step(fr_ctx* ctx, int nsteps, void* stream);
+
+/* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
+ * use for the current surfaces and options).  Bit-identical results. */
+int fr_rk_step_graph(fr_ctx* ctx, int nsteps, void* stream);
+
+/* fr_forces (Section 3.2 mean lift and drag): out[0] = C_L and out[1] = C_D
+ * of the last accumulated step, out[2] = mean C_L, out[3] = mean C_D over
+ * the accumulated steps, out[4] = number of steps.  Synchronises the
+ * context's work.  fr_forces_reset zeroes the running means. */
+int fr_forces(fr_ctx* ctx, int cand, double out[5]);
+int fr_forces_reset(fr_ctx* ctx);
+
+/* Volume integrals in double of the current state of candidate cand:
+ * out[0..nvar-1] = integral of each conserved variable, out[nvar] = kinetic
+ * energy integral (1/2 rho |V|^2).  Used for conservation checks and the
+ * Taylor-Green kinetic-energy history. */
+int fr_integrals(fr_ctx* ctx, int cand, double* out);
+
+/* fwh_register (Section 3.1 permeable data surface): locates npts physical
+ * points xyz (host double [npts][3]) in candidate cand by Newton inversion of
+ * the element maps (lowest element id wins on shared faces) and reserves a
+ * device history of capacity records.  *handle identifies the surface.
+ * Errors: FR_EINVAL (point outside the mesh, bad sizes), FR_ENOMEM. */
+int fwh_register(fr_ctx* ctx, int cand, int npts, const double* xyz, int capacity, int* handle);
+
+/* fwh_sample: appends one record of (rho, V_1..V_3, p) at every point of
+ * surface handle from the current state (FR_EINVAL when full).  Records are
+ * stored as deviations from the free stream in the context precision. */
+int fwh_sample(fr_ctx* ctx, int handle, void* stream);
+
+/* Copies the records of surface handle to out (host double
+ * [nrec][npts][5], total rho, V, p); *nrec gets the record count.  out may
+ * be NULL to query the count.  fwh_clear empties the history. */
+int fwh_history(fr_ctx* ctx, int handle, double* out, int* nrec);
+int fwh_clear(fr_ctx* ctx, int handle);
+
+/* fwh_integrate (Appendix B, Eqs. B.2-B.14, advanced-time approach, on the
+ * data surface repeated ncopies times along z at spacing Lspan, Section
+ * 3.3.1): acoustic pressure p'(t*) at each of nobs observers.
+ * Device inputs (double): hist [nt][npts][5] = (rho, V_1, V_2, V_3, p) at
+ * source times tau0 + k dtau; y [npts][3] panel centres; n [npts][3] outward
+ * unit normals; dS [npts] panel areas.  Host inputs: obs [nobs][3],
+ * Minf[3] (mean-flow Mach vector), c0, rho0, p0.  ncopies must be odd.
+ * Output: p_out (device double [nobs][cap]) receives p'(t*_i) for
+ * i < nt_out[o]; t0_out[o] (host) is the first unified time of observer o;
+ * the unified step is dtau.  The library allocates and frees its own
+ * scratch (one partial-sum row per block of panels).  Errors: FR_EINVAL
+ * (nt < 5, even ncopies, |Minf| >= 1), FR_EWINDOW (empty window for some
+ * observer, or longer than cap), FR_ENOMEM, FR_ECUDA.  Synchronises stream. */
+int fwh_integrate(const double* hist, int nt, int npts, const double* y, const double* n,
+                  const double* dS, double dtau, double tau0, const double* obs, int nobs,
+                  const double Minf[3], double c0, double rho0, double p0, double Lspan,
+                  int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
+                  void* stream);
+
+/* Elements per thread block used by the residual kernels (0 = built-in
+ * default); fr_autotune times the candidates on the current state and keeps
+ * the fastest per kernel, returning it in *best. */
+int fr_set_tile(fr_ctx* ctx, int elems_per_block);
+int fr_autotune(fr_ctx* ctx, int* best);
+
+/* Counts of kernels launched by this context since creation (for
+ * benchmarking claims). */
+int64_t fr_launch_count(const fr_ctx* ctx);
+
+/* Measurement aid: runs nsteps RK4 steps without a graph on stream with a
+ * CUDA event around every launch and returns the summed device time (ms)
+ * per kernel kind in ms_out[0..3] = traces, viscous faces, residual+RK,
+ * forces/sampling, and their launch counts in n_out[0..3].  Advances the
+ * state exactly like fr_rk_step. */
+int fr_profile_step(fr_ctx* ctx, int nsteps, void* stream, double ms_out[4], int64_t n_out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBFR_FR_H */

@@ -1,0 +1,1163 @@
+// libfr C-ABI: context set-up (mesh preprocessing in double on the host),
+// state management, residual / RK4 step launch sequences, CUDA-graph replay,
+// forces, volume integrals and FW-H surface sampling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fr.h"
+#include "fr_common.h"
+#include "fr_geom.h"
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(x)                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) return fail(FR_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL(rc, what)                                                                          \
+    do {                                                                                       \
+        if ((rc) != 0)                                                                         \
+            return fail(FR_ECUDA, std::string(what) + ": " + cudaGetErrorString(cudaError_t(rc))); \
+    } while (0)
+
+namespace {
+
+struct Surface {
+    int cand = 0, npts = 0, cap = 0;
+    int64_t* pe = nullptr;   // element of each point (global index)
+    void* pw = nullptr;      // 1D Lagrange weights [npts][dim][np]
+    void* hist = nullptr;    // [cap][npts][5] deviations from the free stream
+    int* count = nullptr;    // device record counter
+    int* overflow = nullptr;
+};
+
+}  // namespace
+
+struct fr_ctx {
+    int dim = 0, p = 0, np = 0, nsp = 0, nfp = 0, nf = 0, nv = 0;
+    int ncand = 0, prec = 0, visc = 0, kind = 0, affine = 0;
+    int64_t E = 0;
+    fr_options opt{};
+    std::vector<int64_t> cand_off;
+    std::vector<std::vector<double>> nodes;  // per candidate
+    std::vector<int> q;                      // per candidate geometry order
+    frg::Ref1D ref{};
+    size_t rsz = 8;                          // sizeof(Real)
+    // device buffers
+    void *u0 = nullptr, *us = nullptr, *acc = nullptr, *uf = nullptr, *fvn = nullptr;
+    void *S = nullptr, *J = nullptr, *N = nullptr, *ops = nullptr;
+    int32_t* nbr = nullptr;
+    int64_t sS_e = 0, sS_k = 0, sS_sp = 0, sJ_e = 0, sJ_sp = 0, sN_f = 0, sN_fp = 0;
+    int32_t* wall_ef = nullptr;
+    int64_t* wall_off_d = nullptr;
+    std::vector<int64_t> wall_off;
+    double *fnow = nullptr, *fsum = nullptr, *fcnt = nullptr, *partial = nullptr;
+    int partial_blocks = 0;
+    std::vector<Surface> surf;
+    frk::Launch lc[3]{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+    int64_t graph_launches_per_step = 0;
+    int device = 0;
+    double* stage64 = nullptr;  // double staging buffer for FP32 state transfers
+};
+
+namespace {
+
+template <typename Real>
+frk::Geo<Real> geo_of(const fr_ctx* c) {
+    frk::Geo<Real> g;
+    g.S = static_cast<const Real*>(c->S);
+    g.J = static_cast<const Real*>(c->J);
+    g.N = static_cast<const Real*>(c->N);
+    g.nbr = c->nbr;
+    g.sS_e = c->sS_e;
+    g.sS_k = c->sS_k;
+    g.sS_sp = c->sS_sp;
+    g.sJ_e = c->sJ_e;
+    g.sJ_sp = c->sJ_sp;
+    g.sN_f = c->sN_f;
+    g.sN_fp = c->sN_fp;
+    return g;
+}
+
+template <typename Real>
+frk::Phys<Real> phys_of(const fr_ctx* c) {
+    frk::Phys<Real> ph;
+    const fr_options& o = c->opt;
+    ph.gamma = Real(o.gamma);
+    ph.gm1 = Real(o.gamma - 1.0);
+    ph.mu = Real(o.mu);
+    ph.kappa = Real(o.mu * o.gamma / o.prandtl);
+    ph.eta = Real(o.br2_eta);
+    ph.rho_inf = Real(o.rho_inf);
+    ph.p_inf = Real(o.p_inf);
+    for (int i = 0; i < 3; ++i) ph.vel_inf[i] = Real(o.vel_inf[i]);
+    ph.viscous = c->visc;
+    return ph;
+}
+
+template <typename Real>
+frk::Ops<Real> ops_of(const frg::Ref1D& r) {
+    frk::Ops<Real> op;
+    std::memset(&op, 0, sizeof(op));
+    double lhm = 0, lhp = 0;
+    for (int j = 0; j < r.np; ++j) {
+        op.lm[j] = Real(r.lm[j]);
+        op.lp[j] = Real(r.lp[j]);
+        op.hm[j] = Real(r.hm[j]);
+        op.hp[j] = Real(r.hp[j]);
+        op.w[j] = Real(r.w[j]);
+        for (int k = 0; k < r.np; ++k) op.D[j * frk::MAXNP + k] = Real(r.D[j][k]);
+        lhm += r.lm[j] * r.hm[j];
+        lhp += r.lp[j] * r.hp[j];
+    }
+    op.lhm = Real(lhm);
+    op.lhp = Real(lhp);
+    return op;
+}
+
+// ---- dimension dispatch of the per-TU launchers
+template <typename Real>
+int L_traces(fr_ctx* c, const Real* u, cudaStream_t s) {
+    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
+    Real* uf = static_cast<Real*>(c->uf);
+    ++c->launches;
+    return c->dim == 2 ? frl::traces<Real, 2>(c->p, u, uf, c->E, op, c->lc[0], s)
+                       : frl::traces<Real, 3>(c->p, u, uf, c->E, op, c->lc[0], s);
+}
+
+template <typename Real>
+int L_visc(fr_ctx* c, const Real* u, cudaStream_t s) {
+    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
+    const Real* uf = static_cast<const Real*>(c->uf);
+    Real* fvn = static_cast<Real*>(c->fvn);
+    const auto ph = phys_of<Real>(c);
+    const auto g = geo_of<Real>(c);
+    ++c->launches;
+    return c->dim == 2 ? frl::visc_face<Real, 2>(c->p, u, uf, fvn, c->E, op, ph, g, c->lc[1], s)
+                       : frl::visc_face<Real, 3>(c->p, u, uf, fvn, c->E, op, ph, g, c->lc[1], s);
+}
+
+template <typename Real>
+int L_resid(fr_ctx* c, const Real* u, const frk::Stage<Real>& st, cudaStream_t s) {
+    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
+    const Real* uf = static_cast<const Real*>(c->uf);
+    const Real* fvn = static_cast<const Real*>(c->fvn);
+    const auto ph = phys_of<Real>(c);
+    const auto g = geo_of<Real>(c);
+    ++c->launches;
+    return c->dim == 2 ? frl::residual<Real, 2>(c->p, u, uf, fvn, c->E, op, ph, g, st, c->lc[2], s)
+                       : frl::residual<Real, 3>(c->p, u, uf, fvn, c->E, op, ph, g, st, c->lc[2], s);
+}
+
+template <typename Real>
+int L_forces(fr_ctx* c, cudaStream_t s) {
+    if (c->wall_off.empty() || c->wall_off.back() == 0) return 0;
+    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
+    const auto g = geo_of<Real>(c);
+    const Real gm1 = Real(c->opt.gamma - 1.0);
+    ++c->launches;
+    return c->dim == 2
+               ? frl::forces<Real, 2>(c->p, static_cast<const Real*>(c->uf), static_cast<const Real*>(c->fvn),
+                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
+                                      c->fsum, c->fcnt, s)
+               : frl::forces<Real, 3>(c->p, static_cast<const Real*>(c->uf), static_cast<const Real*>(c->fvn),
+                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
+                                      c->fsum, c->fcnt, s);
+}
+
+template <typename Real>
+int L_sample(fr_ctx* c, Surface& sf, cudaStream_t s) {
+    const auto ph = phys_of<Real>(c);
+    c->launches += 2;
+    return c->dim == 2 ? frl::sample<Real, 2>(c->p, static_cast<const Real*>(c->u0), sf.pe,
+                                              static_cast<const Real*>(sf.pw), sf.npts, ph,
+                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.overflow, s)
+                       : frl::sample<Real, 3>(c->p, static_cast<const Real*>(c->u0), sf.pe,
+                                              static_cast<const Real*>(sf.pw), sf.npts, ph,
+                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.overflow, s);
+}
+
+// Optional per-launch event pairs for fr_profile_step: kind 0..3.
+struct Prof {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    cudaStream_t s = nullptr;
+    void mark_begin(int k) {
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, s);
+        ev.push_back(a);
+        kind.push_back(k);
+    }
+    void mark_end() {
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, s);
+        ev.push_back(b);
+    }
+};
+
+template <typename Real>
+int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
+    Real* u0 = static_cast<Real*>(c->u0);
+    Real* us = static_cast<Real*>(c->us);
+    Real* acc = static_cast<Real*>(c->acc);
+    for (int stage = 1; stage <= 4; ++stage) {
+        const Real* in = (stage == 1) ? u0 : us;
+        if (pr) pr->mark_begin(0);
+        int rc = L_traces<Real>(c, in, s);
+        if (pr) pr->mark_end();
+        CKL(rc, "traces kernel");
+        if (c->visc) {
+            if (pr) pr->mark_begin(1);
+            rc = L_visc<Real>(c, in, s);
+            if (pr) pr->mark_end();
+            CKL(rc, "viscous face kernel");
+        }
+        if (stage == 1) {
+            if (pr) pr->mark_begin(3);
+            rc = L_forces<Real>(c, s);
+            CKL(rc, "forces kernel");
+            for (auto& sf : c->surf) {
+                rc = L_sample<Real>(c, sf, s);
+                CKL(rc, "sampling kernel");
+            }
+            if (pr) pr->mark_end();
+        }
+        frk::Stage<Real> st;
+        st.stage = stage;
+        st.dt = Real(c->opt.dt);
+        st.R = nullptr;
+        st.u0 = u0;
+        st.us = us;
+        st.acc = acc;
+        if (pr) pr->mark_begin(2);
+        rc = L_resid<Real>(c, in, st, s);
+        if (pr) pr->mark_end();
+        CKL(rc, "residual kernel");
+    }
+    return FR_OK;
+}
+
+template <typename Real>
+int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
+    int rc = L_traces<Real>(c, u, s);
+    CKL(rc, "traces kernel");
+    if (c->visc) {
+        rc = L_visc<Real>(c, u, s);
+        CKL(rc, "viscous face kernel");
+    }
+    frk::Stage<Real> st;
+    st.stage = 0;
+    st.dt = Real(0);
+    st.R = R;
+    st.u0 = st.us = st.acc = nullptr;
+    rc = L_resid<Real>(c, u, st, s);
+    CKL(rc, "residual kernel");
+    return FR_OK;
+}
+
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        b[i] = float(a[i]);
+}
+__global__ void k_f2d(const float* a, double* b, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        b[i] = double(a[i]);
+}
+
+template <typename T>
+int upload(void** dst, const std::vector<T>& src) {
+    if (src.empty()) { *dst = nullptr; return FR_OK; }
+    if (cudaMalloc(dst, src.size() * sizeof(T)) != cudaSuccess)
+        return fail(FR_ENOMEM, "cudaMalloc failed for a mesh array");
+    CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FR_OK;
+}
+
+int upload_real(void** dst, const std::vector<double>& src, int prec) {
+    if (prec == FR_FP64) return upload(dst, src);
+    std::vector<float> f(src.begin(), src.end());
+    return upload(dst, f);
+}
+
+int orient_map(int dim, int np, int o, int fp) {
+    if (dim == 2) return (o & 1) ? np - 1 - fp : fp;
+    int a = fp % np, b = fp / np;
+    if (o & 4) std::swap(a, b);
+    if (o & 1) a = np - 1 - a;
+    if (o & 2) b = np - 1 - b;
+    return a + np * b;
+}
+
+void default_launch(fr_ctx* c) {
+    const int target = 256;
+    int epb = std::max(1, target / c->nsp);
+    for (int k = 0; k < 3; ++k) {
+        c->lc[k].epb = epb;
+        c->lc[k].threads = target;
+    }
+}
+
+size_t smem_of(const fr_ctx* c, int kernel, int epb) {
+    if (c->prec == FR_FP64)
+        return c->dim == 2 ? frl::smem_bytes<double, 2>(c->p, kernel, epb) : frl::smem_bytes<double, 3>(c->p, kernel, epb);
+    return c->dim == 2 ? frl::smem_bytes<float, 2>(c->p, kernel, epb) : frl::smem_bytes<float, 3>(c->p, kernel, epb);
+}
+
+void release(fr_ctx* c) {
+    if (!c) return;
+    void* bufs[] = {c->u0, c->us, c->acc, c->uf, c->fvn, c->S, c->J, c->N, c->ops, c->nbr,
+                    c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (auto& s : c->surf) {
+        void* sb[] = {s.pe, s.pw, s.hist, s.count, s.overflow};
+        for (void* b : sb)
+            if (b) cudaFree(b);
+    }
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+void invalidate_graph(fr_ctx* c) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+}
+
+}  // namespace
+
+// =====================================================================
+int fr_set_error_from_fwh(int code, const char* msg) { return fail(code, msg); }
+
+extern "C" const char* fr_last_error(void) { return g_err.c_str(); }
+
+extern "C" int fr_ctx_dims(const fr_ctx* c, int64_t out[8]) {
+    if (!c || !out) return fail(FR_EINVAL, "null argument");
+    out[0] = c->dim;
+    out[1] = c->p;
+    out[2] = c->nv;
+    out[3] = c->nsp;
+    out[4] = c->E;
+    out[5] = c->ncand;
+    out[6] = c->prec;
+    out[7] = c->affine;
+    return FR_OK;
+}
+
+extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* o, fr_ctx** out) {
+    if (out) *out = nullptr;
+    if (!m || !o || !out || ncand < 1) return fail(FR_EINVAL, "null argument or ncand < 1");
+    const int dim = m[0].dim;
+    if (dim != 2 && dim != 3) return fail(FR_EINVAL, "dim must be 2 or 3");
+    if (o->order < 1 || o->order > 4) return fail(FR_EINVAL, "order must be 1..4");
+    if (o->precision != FR_FP64 && o->precision != FR_FP32) return fail(FR_EINVAL, "bad precision");
+    if (o->correction != FR_CORR_DG && o->correction != FR_CORR_HUYNH_G2) return fail(FR_EINVAL, "bad correction");
+    if (!(o->gamma > 1.0) || !(o->prandtl > 0.0) || o->mu < 0.0 || !(o->rho_inf > 0.0) || !(o->p_inf > 0.0))
+        return fail(FR_EINVAL, "bad gas or free-stream constants");
+    if (o->viscous && !(o->mu > 0.0)) return fail(FR_EINVAL, "viscous run needs mu > 0");
+    for (int c = 0; c < ncand; ++c) {
+        if (m[c].dim != dim) return fail(FR_EINVAL, "all candidates must share dim");
+        if (m[c].nelem < 1 || !m[c].nodes || !m[c].conn) return fail(FR_EINVAL, "empty mesh");
+        if (m[c].geom_order != 1 && m[c].geom_order != 2) return fail(FR_EINVAL, "geom_order must be 1 or 2");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+        return fail(FR_ECUDA, "no CUDA device available (libfr has no CPU path)");
+
+    fr_ctx* c = new fr_ctx();
+    cudaGetDevice(&c->device);
+    c->dim = dim;
+    c->p = o->order;
+    c->np = c->p + 1;
+    c->nsp = dim == 2 ? c->np * c->np : c->np * c->np * c->np;
+    c->nfp = dim == 2 ? c->np : c->np * c->np;
+    c->nf = 2 * dim;
+    c->nv = dim + 2;
+    c->ncand = ncand;
+    c->prec = o->precision;
+    c->visc = o->viscous ? 1 : 0;
+    c->kind = o->correction;
+    c->opt = *o;
+    if (c->opt.br2_eta == 0.0) c->opt.br2_eta = 1.0;
+    c->rsz = c->prec == FR_FP64 ? 8 : 4;
+    frg::build_ref(c->p, c->kind, c->ref);
+    c->cand_off.assign(ncand + 1, 0);
+    for (int k = 0; k < ncand; ++k) c->cand_off[k + 1] = c->cand_off[k] + m[k].nelem;
+    const int64_t E = c->E = c->cand_off[ncand];
+    const int nsp = c->nsp, nfp = c->nfp, nf = c->nf, nv = c->nv;
+    c->nodes.resize(ncand);
+    c->q.resize(ncand);
+    for (int k = 0; k < ncand; ++k) {
+        const int nq = m[k].geom_order + 1;
+        const int nn = dim == 2 ? nq * nq : nq * nq * nq;
+        c->q[k] = m[k].geom_order;
+        c->nodes[k].assign(m[k].nodes, m[k].nodes + int64_t(m[k].nelem) * nn * dim);
+    }
+
+    // ---- geometry (host, double), parallel over elements
+    std::vector<double> Jh(E * nsp), Sh(E * dim * dim * nsp), Nown(E * nf * nfp * dim);
+    std::vector<int> bad(1, 0);
+    {
+        unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        std::vector<int> badj(nth, 0);
+        for (unsigned t = 0; t < nth; ++t)
+            th.emplace_back([&, t]() {
+                std::vector<double> xsp(nsp * dim);
+                for (int64_t e = t; e < E; e += nth) {
+                    int k = int(std::upper_bound(c->cand_off.begin(), c->cand_off.end(), e) - c->cand_off.begin()) - 1;
+                    const int q = c->q[k];
+                    const int nq = q + 1;
+                    const int nn = dim == 2 ? nq * nq : nq * nq * nq;
+                    const double* nd = c->nodes[k].data() + (e - c->cand_off[k]) * nn * dim;
+                    frg::element_geometry(dim, q, c->ref, nd, xsp.data(), &Jh[e * nsp], &Sh[e * dim * dim * nsp],
+                                          &Nown[e * nf * nfp * dim]);
+                    for (int s = 0; s < nsp; ++s)
+                        if (!(Jh[e * nsp + s] > 0.0)) badj[t] = 1;
+                }
+            });
+        for (auto& x : th) x.join();
+        for (int b : badj) bad[0] |= b;
+    }
+    if (bad[0]) {
+        release(c);
+        return fail(FR_EMESH, "non-positive Jacobian at a solution point");
+    }
+
+    // ---- connectivity, shared normals
+    std::vector<int32_t> nbr(E * nf);
+    std::vector<double> Nsh(Nown);
+    std::vector<std::vector<int32_t>> walls(ncand);
+    for (int k = 0; k < ncand; ++k) {
+        const int64_t off = c->cand_off[k];
+        const int ne = m[k].nelem;
+        const int32_t* cn = m[k].conn;
+        for (int e = 0; e < ne; ++e)
+            for (int f = 0; f < nf; ++f) {
+                const int32_t a = cn[(int64_t(e) * nf + f) * 3 + 0];
+                const int32_t b = cn[(int64_t(e) * nf + f) * 3 + 1];
+                const int32_t oc = cn[(int64_t(e) * nf + f) * 3 + 2];
+                const int64_t ge = off + e;
+                if (a < 0) {
+                    if (a != -FR_BC_WALL && a != -FR_BC_FARFIELD) {
+                        release(c);
+                        return fail(FR_EMESH, "unknown boundary tag");
+                    }
+                    nbr[ge * nf + f] = a;
+                    if (a == -FR_BC_WALL) walls[k].push_back(int32_t(ge * nf + f));
+                    continue;
+                }
+                if (a >= ne || b < 0 || b >= nf || oc < 0 || oc >= (dim == 2 ? 2 : 8)) {
+                    release(c);
+                    return fail(FR_EMESH, "connectivity entry out of range");
+                }
+                const int32_t* back = cn + (int64_t(a) * nf + b) * 3;
+                if (back[0] != e || back[1] != f) {
+                    release(c);
+                    return fail(FR_EMESH, "connectivity is not symmetric");
+                }
+                for (int fp = 0; fp < nfp; ++fp)
+                    if (orient_map(dim, c->np, back[2], orient_map(dim, c->np, oc, fp)) != fp) {
+                        release(c);
+                        return fail(FR_EMESH, "face orientations are not inverse to each other");
+                    }
+                const int64_t gn = off + a;
+                if ((gn * nf + b) * 8 + oc > INT32_MAX) {
+                    release(c);
+                    return fail(FR_EINVAL, "mesh too large for 32-bit face codes");
+                }
+                nbr[ge * nf + f] = int32_t((gn * nf + b) * 8 + oc);
+                // normals: both sides must agree (opposite) -- a mismatch means
+                // the connectivity pairs faces that do not coincide
+                double nmax = 0.0, dmax = 0.0;
+                for (int fp = 0; fp < nfp; ++fp) {
+                    const int fq = orient_map(dim, c->np, oc, fp);
+                    for (int i = 0; i < dim; ++i) {
+                        const double x = Nown[((ge * nf + f) * nfp + fp) * dim + i];
+                        const double y = Nown[((gn * nf + b) * nfp + fq) * dim + i];
+                        nmax = std::max(nmax, std::fabs(x));
+                        dmax = std::max(dmax, std::fabs(x + y));
+                    }
+                }
+                if (dmax > 1e-6 * nmax + 1e-300) {
+                    release(c);
+                    return fail(FR_EMESH, "matched faces have inconsistent normals (wrong connectivity or orientation)");
+                }
+                if (ge * nf + f > gn * nf + b)
+                    for (int fp = 0; fp < nfp; ++fp) {
+                        const int fq = orient_map(dim, c->np, oc, fp);
+                        for (int i = 0; i < dim; ++i)
+                            Nsh[((ge * nf + f) * nfp + fp) * dim + i] = -Nown[((gn * nf + b) * nfp + fq) * dim + i];
+                    }
+            }
+    }
+
+    // ---- affine detection: constant metrics per element and normals per face
+    bool affine = true;
+    for (int64_t e = 0; e < E && affine; ++e) {
+        for (int k = 0; k < dim * dim && affine; ++k) {
+            const double* s = &Sh[(e * dim * dim + k) * nsp];
+            double mx = 0;
+            for (int sp = 0; sp < nsp; ++sp) mx = std::max(mx, std::fabs(s[sp]));
+            for (int sp = 1; sp < nsp; ++sp)
+                if (std::fabs(s[sp] - s[0]) > 1e-13 * (mx + 1e-300)) affine = false;
+        }
+        for (int sp = 1; sp < nsp && affine; ++sp)
+            if (std::fabs(Jh[e * nsp + sp] - Jh[e * nsp]) > 1e-13 * std::fabs(Jh[e * nsp])) affine = false;
+        for (int f = 0; f < nf && affine; ++f)
+            for (int fp = 1; fp < nfp && affine; ++fp)
+                for (int i = 0; i < dim; ++i) {
+                    const double a0 = Nsh[((e * nf + f) * nfp) * dim + i];
+                    const double a1 = Nsh[((e * nf + f) * nfp + fp) * dim + i];
+                    if (std::fabs(a1 - a0) > 1e-13 * (std::fabs(a0) + 1e-300) + 1e-300) affine = false;
+                }
+    }
+    c->affine = affine ? 1 : 0;
+    int rc;
+    if (affine) {
+        std::vector<double> S1(E * dim * dim), J1(E), N1(E * nf * dim);
+        for (int64_t e = 0; e < E; ++e) {
+            for (int k = 0; k < dim * dim; ++k) S1[e * dim * dim + k] = Sh[(e * dim * dim + k) * nsp];
+            J1[e] = Jh[e * nsp];
+            for (int f = 0; f < nf; ++f)
+                for (int i = 0; i < dim; ++i) N1[(e * nf + f) * dim + i] = Nsh[((e * nf + f) * nfp) * dim + i];
+        }
+        c->sS_e = dim * dim; c->sS_k = 1; c->sS_sp = 0;
+        c->sJ_e = 1; c->sJ_sp = 0;
+        c->sN_f = dim; c->sN_fp = 0;
+        if ((rc = upload_real(&c->S, S1, c->prec)) || (rc = upload_real(&c->J, J1, c->prec)) ||
+            (rc = upload_real(&c->N, N1, c->prec))) {
+            release(c);
+            return rc;
+        }
+    } else {
+        c->sS_e = int64_t(dim) * dim * nsp; c->sS_k = nsp; c->sS_sp = 1;
+        c->sJ_e = nsp; c->sJ_sp = 1;
+        c->sN_f = int64_t(nfp) * dim; c->sN_fp = dim;
+        if ((rc = upload_real(&c->S, Sh, c->prec)) || (rc = upload_real(&c->J, Jh, c->prec)) ||
+            (rc = upload_real(&c->N, Nsh, c->prec))) {
+            release(c);
+            return rc;
+        }
+    }
+    if ((rc = upload(reinterpret_cast<void**>(&c->nbr), nbr))) {
+        release(c);
+        return rc;
+    }
+    // walls per candidate
+    std::vector<int32_t> wl;
+    c->wall_off.assign(ncand + 1, 0);
+    for (int k = 0; k < ncand; ++k) {
+        wl.insert(wl.end(), walls[k].begin(), walls[k].end());
+        c->wall_off[k + 1] = int64_t(wl.size());
+    }
+    if ((rc = upload(reinterpret_cast<void**>(&c->wall_ef), wl)) ||
+        (rc = upload(reinterpret_cast<void**>(&c->wall_off_d), c->wall_off))) {
+        release(c);
+        return rc;
+    }
+    // operators
+    if (c->prec == FR_FP64) {
+        auto op = ops_of<double>(c->ref);
+        std::vector<unsigned char> b(sizeof(op));
+        std::memcpy(b.data(), &op, sizeof(op));
+        rc = upload(&c->ops, b);
+    } else {
+        auto op = ops_of<float>(c->ref);
+        std::vector<unsigned char> b(sizeof(op));
+        std::memcpy(b.data(), &op, sizeof(op));
+        rc = upload(&c->ops, b);
+    }
+    if (rc) {
+        release(c);
+        return rc;
+    }
+    // state and trace buffers
+    const size_t nstate = size_t(E) * nv * nsp * c->rsz;
+    const size_t ntrace = size_t(E) * nf * nv * nfp * c->rsz;
+    if (cudaMalloc(&c->u0, nstate) != cudaSuccess || cudaMalloc(&c->us, nstate) != cudaSuccess ||
+        cudaMalloc(&c->acc, nstate) != cudaSuccess || cudaMalloc(&c->uf, ntrace) != cudaSuccess ||
+        cudaMalloc(&c->fvn, ntrace) != cudaSuccess) {
+        release(c);
+        return fail(FR_ENOMEM, "cudaMalloc failed for the state buffers");
+    }
+    cudaMemset(c->u0, 0, nstate);
+    cudaMemset(c->us, 0, nstate);
+    cudaMemset(c->acc, 0, nstate);
+    cudaMemset(c->uf, 0, ntrace);
+    cudaMemset(c->fvn, 0, ntrace);
+    c->partial_blocks = 1024;
+    if (cudaMalloc(&c->fnow, sizeof(double) * 3 * ncand) != cudaSuccess ||
+        cudaMalloc(&c->fsum, sizeof(double) * 3 * ncand) != cudaSuccess ||
+        cudaMalloc(&c->fcnt, sizeof(double) * ncand) != cudaSuccess ||
+        cudaMalloc(&c->partial, sizeof(double) * c->partial_blocks * (nv + 1)) != cudaSuccess) {
+        release(c);
+        return fail(FR_ENOMEM, "cudaMalloc failed for accumulators");
+    }
+    cudaMemset(c->fnow, 0, sizeof(double) * 3 * ncand);
+    cudaMemset(c->fsum, 0, sizeof(double) * 3 * ncand);
+    cudaMemset(c->fcnt, 0, sizeof(double) * ncand);
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        release(c);
+        return fail(FR_ECUDA, "cannot create a stream");
+    }
+    default_launch(c);
+    {
+        // first use of each kernel: shared-memory opt-in outside any capture
+        const int64_t keepE = c->E;
+        c->E = 0;
+        int r0, r1, r2;
+        if (c->prec == FR_FP64) {
+            frk::Stage<double> st{0, 0.0, nullptr, nullptr, nullptr, nullptr};
+            r0 = L_traces<double>(c, nullptr, nullptr);
+            r1 = L_visc<double>(c, nullptr, nullptr);
+            r2 = L_resid<double>(c, nullptr, st, nullptr);
+        } else {
+            frk::Stage<float> st{0, 0.0f, nullptr, nullptr, nullptr, nullptr};
+            r0 = L_traces<float>(c, nullptr, nullptr);
+            r1 = L_visc<float>(c, nullptr, nullptr);
+            r2 = L_resid<float>(c, nullptr, st, nullptr);
+        }
+        c->E = keepE;
+        c->launches = 0;
+        if (r0 || r1 || r2) {
+            release(c);
+            return fail(FR_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(cudaError_t(r0 | r1 | r2)));
+        }
+    }
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        release(c);
+        return fail(FR_ECUDA, std::string("set-up: ") + cudaGetErrorString(err));
+    }
+    *out = c;
+    return FR_OK;
+}
+
+extern "C" int fr_destroy(fr_ctx* c) {
+    if (!c) return FR_OK;
+    cudaDeviceSynchronize();
+    release(c);
+    return FR_OK;
+}
+
+extern "C" int fr_cand_range(const fr_ctx* c, int cand, int64_t* first, int64_t* count) {
+    if (!c || !first || !count) return fail(FR_EINVAL, "null argument");
+    if (cand < 0) {
+        *first = 0;
+        *count = c->E;
+        return FR_OK;
+    }
+    if (cand >= c->ncand) return fail(FR_EINVAL, "candidate out of range");
+    *first = c->cand_off[cand];
+    *count = c->cand_off[cand + 1] - c->cand_off[cand];
+    return FR_OK;
+}
+
+extern "C" int fr_sp_coords(const fr_ctx* c, int cand, double* xyz) {
+    if (!c || !xyz) return fail(FR_EINVAL, "null argument");
+    int64_t first, count;
+    int rc = fr_cand_range(c, cand, &first, &count);
+    if (rc) return rc;
+    const int dim = c->dim, nsp = c->nsp, nf = c->nf, nfp = c->nfp;
+    std::vector<double> J(nsp), S(dim * dim * nsp), N(nf * nfp * dim);
+    for (int64_t e = first; e < first + count; ++e) {
+        int k = int(std::upper_bound(c->cand_off.begin(), c->cand_off.end(), e) - c->cand_off.begin()) - 1;
+        const int nq = c->q[k] + 1;
+        const int nn = dim == 2 ? nq * nq : nq * nq * nq;
+        frg::element_geometry(dim, c->q[k], c->ref, c->nodes[k].data() + (e - c->cand_off[k]) * nn * dim,
+                              xyz + (e - first) * nsp * dim, J.data(), S.data(), N.data());
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_state_set(fr_ctx* c, int cand, const double* u, int on_device, void* stream) {
+    if (!c || !u) return fail(FR_EINVAL, "null argument");
+    int64_t first, count;
+    int rc = fr_cand_range(c, cand, &first, &count);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = count * c->nv * c->nsp;
+    char* dst = static_cast<char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
+    if (c->prec == FR_FP64) {
+        CK(cudaMemcpyAsync(dst, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    } else if (on_device) {
+        k_d2f<<<1024, 256, 0, s>>>(u, reinterpret_cast<float*>(dst), n);
+        ++c->launches;
+        CK(cudaGetLastError());
+    } else {
+        // host doubles -> device staging -> float on the device
+        if (!c->stage64 && cudaMalloc(&c->stage64, size_t(c->E) * c->nv * c->nsp * 8) != cudaSuccess) {
+            c->stage64 = nullptr;
+            return fail(FR_ENOMEM, "cannot allocate the transfer staging buffer");
+        }
+        CK(cudaMemcpyAsync(c->stage64, u, n * 8, cudaMemcpyHostToDevice, s));
+        k_d2f<<<1024, 256, 0, s>>>(c->stage64, reinterpret_cast<float*>(dst), n);
+        ++c->launches;
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(s));
+    return FR_OK;
+}
+
+extern "C" int fr_state_get(fr_ctx* c, int cand, double* u, int on_device, void* stream) {
+    if (!c || !u) return fail(FR_EINVAL, "null argument");
+    int64_t first, count;
+    int rc = fr_cand_range(c, cand, &first, &count);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = count * c->nv * c->nsp;
+    const char* src = static_cast<const char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
+    if (c->prec == FR_FP64) {
+        CK(cudaMemcpyAsync(u, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else if (on_device) {
+        k_f2d<<<1024, 256, 0, s>>>(reinterpret_cast<const float*>(src), u, n);
+        ++c->launches;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+    } else {
+        if (!c->stage64 && cudaMalloc(&c->stage64, size_t(c->E) * c->nv * c->nsp * 8) != cudaSuccess) {
+            c->stage64 = nullptr;
+            return fail(FR_ENOMEM, "cannot allocate the transfer staging buffer");
+        }
+        k_f2d<<<1024, 256, 0, s>>>(reinterpret_cast<const float*>(src), c->stage64, n);
+        ++c->launches;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(u, c->stage64, n * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!std::isfinite(u[i])) return fail(FR_ENONFINITE, "state holds NaN or Inf");
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_residual(fr_ctx* c, const void* u, void* R, void* stream) {
+    if (!c || !u || !R) return fail(FR_EINVAL, "null argument");
+    if (u == R) return fail(FR_EINVAL, "u and R must not overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->prec == FR_FP64)
+        return enqueue_residual<double>(c, static_cast<const double*>(u), static_cast<double*>(R), s);
+    return enqueue_residual<float>(c, static_cast<const float*>(u), static_cast<float*>(R), s);
+}
+
+extern "C" int fr_rk_step(fr_ctx* c, int nsteps, void* stream) {
+    if (!c || nsteps < 0) return fail(FR_EINVAL, "bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < nsteps; ++k) {
+        const int rc = c->prec == FR_FP64 ? enqueue_step<double>(c, s) : enqueue_step<float>(c, s);
+        if (rc) return rc;
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_rk_step_graph(fr_ctx* c, int nsteps, void* stream) {
+    if (!c || nsteps < 0) return fail(FR_EINVAL, "bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!c->gexec) {
+        // make sure every kernel attribute is set before capture
+        CK(cudaStreamSynchronize(s));
+        const int64_t before = c->launches;
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = c->prec == FR_FP64 ? enqueue_step<double>(c, c->cap_stream)
+                                          : enqueue_step<float>(c, c->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ec != cudaSuccess) return fail(FR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(FR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        c->graph_launches_per_step = c->launches - before;
+        c->launches = before;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(c->gexec, s));
+        c->launches += c->graph_launches_per_step;
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_forces(fr_ctx* c, int cand, double out[5]) {
+    if (!c || !out || cand < 0 || cand >= c->ncand) return fail(FR_EINVAL, "bad argument");
+    CK(cudaDeviceSynchronize());
+    double fnow[3], fsum[3], cnt;
+    CK(cudaMemcpy(fnow, c->fnow + 3 * cand, sizeof(fnow), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(fsum, c->fsum + 3 * cand, sizeof(fsum), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&cnt, c->fcnt + cand, sizeof(double), cudaMemcpyDeviceToHost));
+    const fr_options& o = c->opt;
+    double v2 = 0;
+    for (int i = 0; i < c->dim; ++i) v2 += o.vel_inf[i] * o.vel_inf[i];
+    const double qa = 0.5 * o.rho_inf * v2 * o.ref_area;
+    if (!(qa > 0.0)) return fail(FR_EINVAL, "force coefficients need |V_inf| > 0 and ref_area > 0");
+    double cl = 0, cd = 0, ml = 0, md = 0;
+    for (int i = 0; i < c->dim; ++i) {
+        cl += fnow[i] * o.lift_dir[i];
+        cd += fnow[i] * o.drag_dir[i];
+        ml += fsum[i] * o.lift_dir[i];
+        md += fsum[i] * o.drag_dir[i];
+    }
+    out[0] = cl / qa;
+    out[1] = cd / qa;
+    out[2] = cnt > 0 ? ml / (qa * cnt) : 0.0;
+    out[3] = cnt > 0 ? md / (qa * cnt) : 0.0;
+    out[4] = cnt;
+    return FR_OK;
+}
+
+extern "C" int fr_forces_reset(fr_ctx* c) {
+    if (!c) return fail(FR_EINVAL, "null argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(c->fsum, 0, sizeof(double) * 3 * c->ncand));
+    CK(cudaMemset(c->fcnt, 0, sizeof(double) * c->ncand));
+    return FR_OK;
+}
+
+extern "C" int fr_integrals(fr_ctx* c, int cand, double* out) {
+    if (!c || !out) return fail(FR_EINVAL, "null argument");
+    int64_t first, count;
+    int rc = fr_cand_range(c, cand, &first, &count);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    const int nb = int(std::min<int64_t>(c->partial_blocks, std::max<int64_t>(1, (count * c->nsp + 255) / 256)));
+    if (c->prec == FR_FP64) {
+        auto g = geo_of<double>(c);
+        auto op = static_cast<const frk::Ops<double>*>(c->ops);
+        rc = c->dim == 2 ? frl::integrals<double, 2>(c->p, static_cast<const double*>(c->u0), first, count, op, g,
+                                                     c->partial, nb, nullptr)
+                         : frl::integrals<double, 3>(c->p, static_cast<const double*>(c->u0), first, count, op, g,
+                                                     c->partial, nb, nullptr);
+    } else {
+        auto g = geo_of<float>(c);
+        auto op = static_cast<const frk::Ops<float>*>(c->ops);
+        rc = c->dim == 2 ? frl::integrals<float, 2>(c->p, static_cast<const float*>(c->u0), first, count, op, g,
+                                                    c->partial, nb, nullptr)
+                         : frl::integrals<float, 3>(c->p, static_cast<const float*>(c->u0), first, count, op, g,
+                                                    c->partial, nb, nullptr);
+    }
+    ++c->launches;
+    CKL(rc, "integrals kernel");
+    std::vector<double> h(size_t(nb) * (c->nv + 1));
+    CK(cudaMemcpy(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int v = 0; v <= c->nv; ++v) {
+        double s = 0;
+        for (int b = 0; b < nb; ++b) s += h[size_t(b) * (c->nv + 1) + v];
+        out[v] = s;
+    }
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------- FW-H surfaces
+extern "C" int fwh_register(fr_ctx* c, int cand, int npts, const double* xyz, int capacity, int* handle) {
+    if (!c || !xyz || !handle || npts < 1 || capacity < 1 || cand < 0 || cand >= c->ncand)
+        return fail(FR_EINVAL, "bad argument");
+    const int dim = c->dim;
+    const int q = c->q[cand];
+    const int nq = q + 1;
+    const int nn = dim == 2 ? nq * nq : nq * nq * nq;
+    const int64_t ne = c->cand_off[cand + 1] - c->cand_off[cand];
+    const double* nodes = c->nodes[cand].data();
+    // element bounding boxes, binned on a uniform grid
+    std::vector<double> lo(ne * dim), hi(ne * dim);
+    double glo[3] = {1e300, 1e300, 1e300}, ghi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t e = 0; e < ne; ++e)
+        for (int i = 0; i < dim; ++i) {
+            double a = 1e300, b = -1e300;
+            for (int k = 0; k < nn; ++k) {
+                a = std::min(a, nodes[(e * nn + k) * dim + i]);
+                b = std::max(b, nodes[(e * nn + k) * dim + i]);
+            }
+            const double pad = 0.05 * (b - a) + 1e-12;
+            lo[e * dim + i] = a - pad;
+            hi[e * dim + i] = b + pad;
+            glo[i] = std::min(glo[i], a - pad);
+            ghi[i] = std::max(ghi[i], b + pad);
+        }
+    const int G = std::max(1, int(std::pow(double(ne), 1.0 / dim)));
+    auto cell = [&](int i, double x) {
+        int k = int((x - glo[i]) / (ghi[i] - glo[i]) * G);
+        return std::min(G - 1, std::max(0, k));
+    };
+    const int ncell = dim == 2 ? G * G : G * G * G;
+    std::vector<std::vector<int64_t>> bins(ncell);
+    for (int64_t e = 0; e < ne; ++e) {
+        int a[3], b[3];
+        for (int i = 0; i < 3; ++i) { a[i] = 0; b[i] = 0; }
+        for (int i = 0; i < dim; ++i) {
+            a[i] = cell(i, lo[e * dim + i]);
+            b[i] = cell(i, hi[e * dim + i]);
+        }
+        for (int z = a[2]; z <= b[2]; ++z)
+            for (int y = a[1]; y <= b[1]; ++y)
+                for (int x = a[0]; x <= b[0]; ++x) bins[(z * G + y) * G + x].push_back(e);
+    }
+    std::vector<int64_t> pe(npts);
+    std::vector<double> pw(size_t(npts) * dim * c->np);
+    for (int k = 0; k < npts; ++k) {
+        const double* y = xyz + size_t(k) * 3;
+        int ci[3] = {0, 0, 0};
+        for (int i = 0; i < dim; ++i) ci[i] = cell(i, y[i]);
+        const auto& list = bins[(ci[2] * G + ci[1]) * G + ci[0]];
+        int64_t found = -1;
+        double xi[3] = {0, 0, 0};
+        for (int64_t e : list) {
+            bool inside = true;
+            for (int i = 0; i < dim; ++i)
+                if (y[i] < lo[e * dim + i] || y[i] > hi[e * dim + i]) inside = false;
+            if (!inside) continue;
+            double t[3] = {0, 0, 0};
+            bool ok = false;
+            for (int it = 0; it < 50; ++it) {
+                double x[3], A[9];
+                frg::element_map(dim, q, nodes + e * nn * dim, t, x, A);
+                double r[3] = {y[0] - x[0], y[1] - x[1], dim == 3 ? y[2] - x[2] : 0.0};
+                double d[3];
+                if (dim == 2) {
+                    const double det = A[0] * A[3] - A[1] * A[2];
+                    d[0] = (A[3] * r[0] - A[1] * r[1]) / det;
+                    d[1] = (-A[2] * r[0] + A[0] * r[1]) / det;
+                } else {
+                    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+                    d[0] = (r[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (r[1] * A[8] - A[5] * r[2]) +
+                            A[2] * (r[1] * A[7] - A[4] * r[2])) / det;
+                    d[1] = (A[0] * (r[1] * A[8] - A[5] * r[2]) - r[0] * (A[3] * A[8] - A[5] * A[6]) +
+                            A[2] * (A[3] * r[2] - r[1] * A[6])) / det;
+                    d[2] = (A[0] * (A[4] * r[2] - r[1] * A[7]) - A[1] * (A[3] * r[2] - r[1] * A[6]) +
+                            r[0] * (A[3] * A[7] - A[4] * A[6])) / det;
+                }
+                double dm = 0, tm = 0;
+                for (int i = 0; i < dim; ++i) {
+                    t[i] += d[i];
+                    dm = std::max(dm, std::fabs(d[i]));
+                    tm = std::max(tm, std::fabs(t[i]));
+                }
+                if (!(tm < 3.0)) break;
+                if (dm < 1e-13) {
+                    ok = true;
+                    break;
+                }
+            }
+            bool in = ok;
+            for (int i = 0; i < dim; ++i) in = in && std::fabs(t[i]) <= 1.0 + 1e-10;
+            if (in) {
+                found = e;
+                for (int i = 0; i < dim; ++i) xi[i] = std::max(-1.0, std::min(1.0, t[i]));
+                break;
+            }
+        }
+        if (found < 0) return fail(FR_EINVAL, "surface point " + std::to_string(k) + " is outside the mesh");
+        pe[k] = c->cand_off[cand] + found;
+        for (int i = 0; i < dim; ++i)
+            for (int j = 0; j < c->np; ++j)
+                pw[(size_t(k) * dim + i) * c->np + j] = frg::lagrange(c->ref.x, c->np, j, xi[i]);
+    }
+    Surface sf;
+    sf.cand = cand;
+    sf.npts = npts;
+    sf.cap = capacity;
+    int rc;
+    if ((rc = upload(reinterpret_cast<void**>(&sf.pe), pe)) || (rc = upload_real(&sf.pw, pw, c->prec))) return rc;
+    if (cudaMalloc(&sf.hist, size_t(capacity) * npts * 5 * c->rsz) != cudaSuccess ||
+        cudaMalloc(&sf.count, sizeof(int)) != cudaSuccess || cudaMalloc(&sf.overflow, sizeof(int)) != cudaSuccess) {
+        if (sf.hist) cudaFree(sf.hist);
+        if (sf.count) cudaFree(sf.count);
+        cudaFree(sf.pe);
+        cudaFree(sf.pw);
+        return fail(FR_ENOMEM, "cannot allocate the FW-H history");
+    }
+    CK(cudaMemset(sf.count, 0, sizeof(int)));
+    CK(cudaMemset(sf.overflow, 0, sizeof(int)));
+    c->surf.push_back(sf);
+    invalidate_graph(c);
+    *handle = int(c->surf.size()) - 1;
+    return FR_OK;
+}
+
+extern "C" int fwh_sample(fr_ctx* c, int handle, void* stream) {
+    if (!c || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad surface handle");
+    Surface& sf = c->surf[handle];
+    int cnt = 0;
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    CK(cudaMemcpy(&cnt, sf.count, sizeof(int), cudaMemcpyDeviceToHost));
+    if (cnt >= sf.cap) return fail(FR_EINVAL, "FW-H history is full");
+    const int rc = c->prec == FR_FP64 ? L_sample<double>(c, sf, static_cast<cudaStream_t>(stream))
+                                      : L_sample<float>(c, sf, static_cast<cudaStream_t>(stream));
+    CKL(rc, "sampling kernel");
+    return FR_OK;
+}
+
+extern "C" int fwh_history(fr_ctx* c, int handle, double* out, int* nrec) {
+    if (!c || !nrec || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad argument");
+    Surface& sf = c->surf[handle];
+    CK(cudaDeviceSynchronize());
+    int cnt = 0, over = 0;
+    CK(cudaMemcpy(&cnt, sf.count, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&over, sf.overflow, sizeof(int), cudaMemcpyDeviceToHost));
+    *nrec = cnt;
+    if (!out) return over ? fail(FR_EINVAL, "FW-H history overflowed") : FR_OK;
+    const size_t n = size_t(cnt) * sf.npts * 5;
+    std::vector<double> h(n);
+    if (c->prec == FR_FP64) {
+        CK(cudaMemcpy(h.data(), sf.hist, n * 8, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> f(n);
+        CK(cudaMemcpy(f.data(), sf.hist, n * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) h[i] = f[i];
+    }
+    const fr_options& o = c->opt;
+    for (size_t r = 0; r < size_t(cnt) * sf.npts; ++r) {
+        out[r * 5 + 0] = h[r * 5 + 0] + o.rho_inf;
+        for (int i = 0; i < 3; ++i) out[r * 5 + 1 + i] = h[r * 5 + 1 + i] + (i < c->dim ? o.vel_inf[i] : 0.0);
+        out[r * 5 + 4] = h[r * 5 + 4] + o.p_inf;
+    }
+    return over ? fail(FR_EINVAL, "FW-H history overflowed") : FR_OK;
+}
+
+extern "C" int fwh_clear(fr_ctx* c, int handle) {
+    if (!c || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad surface handle");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(c->surf[handle].count, 0, sizeof(int)));
+    CK(cudaMemset(c->surf[handle].overflow, 0, sizeof(int)));
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------- tiles
+extern "C" int fr_set_tile(fr_ctx* c, int epb) {
+    if (!c || epb < 0 || epb > 64) return fail(FR_EINVAL, "bad tile");
+    if (epb == 0) {
+        default_launch(c);
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            if (smem_of(c, k, epb) > 227 * 1024) return fail(FR_EINVAL, "tile needs too much shared memory");
+            c->lc[k].epb = epb;
+            c->lc[k].threads = std::min(512, std::max(64, ((epb * c->nsp + 31) / 32) * 32));
+        }
+    }
+    invalidate_graph(c);
+    return FR_OK;
+}
+
+extern "C" int fr_autotune(fr_ctx* c, int* best) {
+    if (!c) return fail(FR_EINVAL, "null argument");
+    // time each kernel for candidate tiles on the current state; keep the fastest
+    const int cand[] = {1, 2, 4, 8, 16};
+    const int threads_opts[] = {128, 256, 512};
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    frk::Launch bestl[3] = {c->lc[0], c->lc[1], c->lc[2]};
+    float bestt[3] = {1e30f, 1e30f, 1e30f};
+    void* R = nullptr;
+    const size_t nstate = size_t(c->E) * c->nv * c->nsp * c->rsz;
+    if (cudaMalloc(&R, nstate) != cudaSuccess) return fail(FR_ENOMEM, "autotune scratch");
+    const frk::Launch saved[3] = {c->lc[0], c->lc[1], c->lc[2]};
+    for (int epb : cand) {
+        for (int th : threads_opts) {
+            if (th > 1024) continue;
+            bool fits = true;
+            for (int k = 0; k < 3; ++k) fits = fits && smem_of(c, k, epb) <= 200 * 1024;
+            if (!fits) continue;
+            for (int k = 0; k < 3; ++k) c->lc[k] = frk::Launch{epb, th};
+            // warm-up then time each kernel separately (5 reps)
+            for (int kern = 0; kern < 3; ++kern) {
+                if (kern == 1 && !c->visc) continue;
+                float tot = 0;
+                for (int rep = 0; rep < 6; ++rep) {
+                    CK(cudaEventRecord(a, nullptr));
+                    int rc = 0;
+                    if (c->prec == FR_FP64) {
+                        const double* u = static_cast<const double*>(c->u0);
+                        if (kern == 0) rc = L_traces<double>(c, u, nullptr);
+                        else if (kern == 1) rc = L_visc<double>(c, u, nullptr);
+                        else {
+                            frk::Stage<double> st{0, 0.0, static_cast<double*>(R), nullptr, nullptr, nullptr};
+                            rc = L_resid<double>(c, u, st, nullptr);
+                        }
+                    } else {
+                        const float* u = static_cast<const float*>(c->u0);
+                        if (kern == 0) rc = L_traces<float>(c, u, nullptr);
+                        else if (kern == 1) rc = L_visc<float>(c, u, nullptr);
+                        else {
+                            frk::Stage<float> st{0, 0.0f, static_cast<float*>(R), nullptr, nullptr, nullptr};
+                            rc = L_resid<float>(c, u, st, nullptr);
+                        }
+                    }
+                    CK(cudaEventRecord(b, nullptr));
+                    CK(cudaEventSynchronize(b));
+                    if (rc) break;
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, a, b);
+                    if (rep > 0) tot += ms;
+                }
+                if (tot > 0 && tot < bestt[kern]) {
+                    bestt[kern] = tot;
+                    bestl[kern] = frk::Launch{epb, th};
+                }
+            }
+        }
+    }
+    (void)saved;
+    for (int k = 0; k < 3; ++k) c->lc[k] = bestl[k];
+    cudaFree(R);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    invalidate_graph(c);
+    if (best) *best = c->lc[2].epb;
+    return FR_OK;
+}
+
+extern "C" int64_t fr_launch_count(const fr_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_out[4], int64_t n_out[4]) {
+    if (!c || nsteps < 0 || !ms_out || !n_out) return fail(FR_EINVAL, "bad argument");
+    Prof pr;
+    pr.s = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < 4; ++k) {
+        ms_out[k] = 0.0;
+        n_out[k] = 0;
+    }
+    int rc = FR_OK;
+    for (int k = 0; k < nsteps && rc == FR_OK; ++k)
+        rc = c->prec == FR_FP64 ? enqueue_step<double>(c, pr.s, &pr) : enqueue_step<float>(c, pr.s, &pr);
+    cudaError_t e = cudaStreamSynchronize(pr.s);
+    for (size_t i = 0; i < pr.kind.size() && 2 * i + 1 < pr.ev.size(); ++i) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]);
+        ms_out[pr.kind[i]] += ms;
+        n_out[pr.kind[i]] += 1;
+    }
+    for (auto ev : pr.ev) cudaEventDestroy(ev);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(FR_ECUDA, cudaGetErrorString(e));
+    return FR_OK;
+}

@@ -1,0 +1,114 @@
+// Shared declarations of the libfr host code and kernels (not part of the
+// public ABI).  Plain structs passed to kernels by value.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "fr.h"
+
+namespace frk {
+
+constexpr int MAXNP = 5;  // p <= 4
+
+// 1D reference operators of one order p and correction kind, Section 1 (FR):
+// lm/lp extrapolate a line of solution points to the xi=-1/+1 end, D is the
+// solution-point derivative matrix D[i*MAXNP+j] = l_j'(x_i), hm/hp are the
+// correction-derivative profiles (-g_L'(x_i) and g_R'(x_i)), w the GL
+// weights; lhm/lhp = sum_j lm_j hm_j and sum_j lp_j hp_j.
+template <typename Real>
+struct Ops {
+    Real lm[MAXNP];
+    Real lp[MAXNP];
+    Real D[MAXNP * MAXNP];
+    Real hm[MAXNP];
+    Real hp[MAXNP];
+    Real w[MAXNP];
+    Real lhm, lhp;
+};
+
+// Gas and flow constants (Section 2.1, Eqs. 5-7) and the free stream.
+template <typename Real>
+struct Phys {
+    Real gamma, gm1, mu, kappa, eta;
+    Real rho_inf, p_inf, vel_inf[3];
+    int viscous;
+};
+
+// Geometry arrays with strides: an affine mesh stores one metric set per
+// element (sp/fp strides 0), a curved mesh one per solution/flux point.
+//   S[e*sS_e + k*sS_k + sp*sS_sp], k = d*DIM + i   : |J| dxi_d/dx_i
+//   J[e*sJ_e + sp*sJ_sp]                            : |J|
+//   N[(e*NF + f)*sN_f + fp*sN_fp + i]               : outward area-weighted normal
+//   nbr[e*NF + f] = (ne*NF + nf)*8 + orientation, or -tag on boundary faces
+template <typename Real>
+struct Geo {
+    const Real* S;
+    const Real* J;
+    const Real* N;
+    const int32_t* nbr;
+    int64_t sS_e, sS_k, sS_sp;
+    int64_t sJ_e, sJ_sp;
+    int64_t sN_f, sN_fp;
+};
+
+// RK4 stage control for the fused residual/update kernel.
+//   stage 0: write R only (fr_residual)
+//   stage 1: input u0;  acc = dt/6 k1;        us = u0 + dt/2 k1
+//   stage 2: input us;  acc += dt/3 k2;       us = u0 + dt/2 k2
+//   stage 3: input us;  acc += dt/3 k3;       us = u0 + dt k3
+//   stage 4: input us;  u0 = u0 + acc + dt/6 k4
+template <typename Real>
+struct Stage {
+    int stage;
+    Real dt;
+    Real* R;          // stage 0 output
+    Real* u0;
+    Real* us;
+    Real* acc;
+};
+
+struct Launch {
+    int epb;          // elements per block
+    int threads;      // threads per block
+};
+
+}  // namespace frk
+
+// Host-side launchers implemented per precision and dimension.
+namespace frl {
+
+// Each returns a cudaError_t value (0 on success).  `op` is a device pointer
+// to the Ops of the context's order and correction.
+template <typename Real, int DIM>
+int traces(int P, const Real* u, Real* uf, int64_t E, const frk::Ops<Real>* op,
+           frk::Launch lc, void* stream);
+
+template <typename Real, int DIM>
+int visc_face(int P, const Real* u, const Real* uf, Real* fvn, int64_t E,
+              const frk::Ops<Real>* op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
+              frk::Launch lc, void* stream);
+
+template <typename Real, int DIM>
+int residual(int P, const Real* u, const Real* uf, const Real* fvn, int64_t E,
+             const frk::Ops<Real>* op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
+             const frk::Stage<Real>& st, frk::Launch lc, void* stream);
+
+template <typename Real, int DIM>
+int forces(int P, const Real* uf, const Real* fvn, const int32_t* wall_ef, const int64_t* wall_off,
+           int ncand, const frk::Ops<Real>* op, const frk::Geo<Real>& g, Real gm1, int viscous,
+           double* fnow, double* fsum, double* fcnt, void* stream);
+
+template <typename Real, int DIM>
+int sample(int P, const Real* u, const int64_t* pe, const Real* pw, int npts, const frk::Phys<Real>& ph,
+           Real* hist, int* count, int cap, int* overflow, void* stream);
+
+template <typename Real, int DIM>
+int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>* op,
+              const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
+
+// dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual)
+template <typename Real, int DIM>
+size_t smem_bytes(int P, int kernel, int epb);
+
+}  // namespace frl

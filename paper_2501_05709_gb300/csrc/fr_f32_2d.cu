@@ -1,0 +1,4 @@
+// FR kernels instantiated for float in 2D.
+#define FR_REAL float
+#define FR_DIM 2
+#include "fr_launch.cuh"

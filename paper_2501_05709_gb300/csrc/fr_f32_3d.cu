@@ -1,0 +1,4 @@
+// FR kernels instantiated for float in 3D.
+#define FR_REAL float
+#define FR_DIM 3
+#include "fr_launch.cuh"

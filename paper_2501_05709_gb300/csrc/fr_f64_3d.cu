@@ -1,0 +1,4 @@
+// FR kernels instantiated for double in 3D.
+#define FR_REAL double
+#define FR_DIM 3
+#include "fr_launch.cuh"

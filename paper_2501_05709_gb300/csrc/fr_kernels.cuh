@@ -1,0 +1,847 @@
+// Flux Reconstruction kernels for sm_103a, templated on dimension, order and
+// precision.  One thread block processes a tile of `epb` whole elements; the
+// element data are staged in shared memory and every phase is a block-wide
+// loop over solution points or face points, separated by __syncthreads().
+//
+// Per RK stage three sweeps (the two BR2 neighbour dependencies force them):
+//   k_traces     u            -> u_f (flux-point traces, written for neighbours)
+//   k_visc_face  u, u_f(nbr)  -> own-side viscous normal flux at flux points
+//   k_residual   u, u_f(nbr), viscous fluxes(own, nbr) -> R, fused RK4 stage
+// Notation and steps follow Section 2.1 (Eqs. 1-7) with the FR reading
+// described in fr_common.h / fr.h: GL points, DG or g2 correction, Rusanov,
+// BR2, metric terms S = |J| dxi/dx in conservative-curl form.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fr_common.h"
+
+namespace frk {
+
+template <int DIM, int P>
+struct Sz {
+    static constexpr int NP = P + 1;
+    static constexpr int NSP = (DIM == 2) ? NP * NP : NP * NP * NP;
+    static constexpr int NFP = (DIM == 2) ? NP : NP * NP;
+    static constexpr int NF = 2 * DIM;
+    static constexpr int NV = DIM + 2;
+};
+
+// solution point j (along direction d) of the line through face point fp of a
+// face normal to d; face points enumerate the remaining directions in
+// increasing order, the lower one fastest
+template <int DIM, int NP>
+__device__ __forceinline__ int line_sp(int d, int fp, int j) {
+    if (DIM == 2) return d == 0 ? j + NP * fp : fp + NP * j;
+    const int a = fp % NP, b = fp / NP;
+    if (d == 0) return j + NP * (a + NP * b);
+    if (d == 1) return a + NP * (j + NP * b);
+    return a + NP * (b + NP * j);
+}
+
+// inverse of line_sp for direction d: face point and position along the line
+template <int DIM, int NP>
+__device__ __forceinline__ void sp_split(int sp, int d, int& fp, int& j) {
+    if (DIM == 2) {
+        const int i0 = sp % NP, i1 = sp / NP;
+        if (d == 0) { j = i0; fp = i1; } else { j = i1; fp = i0; }
+        return;
+    }
+    const int i0 = sp % NP, i1 = (sp / NP) % NP, i2 = sp / (NP * NP);
+    if (d == 0) { j = i0; fp = i1 + NP * i2; }
+    else if (d == 1) { j = i1; fp = i0 + NP * i2; }
+    else { j = i2; fp = i0 + NP * i1; }
+}
+
+// neighbour face point matching face point fp for orientation code o
+template <int DIM, int NP>
+__device__ __forceinline__ int omap(int o, int fp) {
+    if (DIM == 2) return (o & 1) ? NP - 1 - fp : fp;
+    int a = fp % NP, b = fp / NP;
+    if (o & 4) { const int t = a; a = b; b = t; }
+    if (o & 1) a = NP - 1 - a;
+    if (o & 2) b = NP - 1 - b;
+    return a + NP * b;
+}
+
+// ---------------------------------------------------------------- physics
+template <int DIM, typename Real>
+__device__ __forceinline__ Real pressure(const Real* u, Real gm1) {
+    Real m2 = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) m2 += u[1 + i] * u[1 + i];
+    return gm1 * (u[DIM + 1] - Real(0.5) * m2 / u[0]);
+}
+
+// normal component F_inv(u).n of Eq. 3 for any vector n
+template <int DIM, typename Real>
+__device__ __forceinline__ void flux_inv_n(const Real* u, Real p, const Real* n, Real* Fn) {
+    Real mn = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) mn += u[1 + i] * n[i];
+    const Real vn = mn / u[0];
+    Fn[0] = mn;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) Fn[1 + i] = u[1 + i] * vn + p * n[i];
+    Fn[DIM + 1] = (u[DIM + 1] + p) * vn;
+}
+
+// Rusanov common flux, area-weighted: F^c.N = |N| [ (F_L + F_R).n/2 - lambda (u_R - u_L)/2 ],
+// lambda = max(|V_L.n| + c_L, |V_R.n| + c_R)
+template <int DIM, typename Real>
+__device__ __forceinline__ void rusanov(const Real* uL, const Real* uR, const Real* N,
+                                        Real gamma, Real gm1, Real* F) {
+    constexpr int NV = DIM + 2;
+    Real a2 = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) a2 += N[i] * N[i];
+    const Real area = sqrt(a2);
+    Real n[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) n[i] = N[i] / area;
+    const Real pL = pressure<DIM>(uL, gm1), pR = pressure<DIM>(uR, gm1);
+    Real FL[NV], FR[NV];
+    flux_inv_n<DIM>(uL, pL, n, FL);
+    flux_inv_n<DIM>(uR, pR, n, FR);
+    const Real vL = fabs(FL[0] / uL[0]);
+    const Real vR = fabs(FR[0] / uR[0]);
+    const Real cL = sqrt(gamma * pL / uL[0]);
+    const Real cR = sqrt(gamma * pR / uR[0]);
+    const Real lam = fmax(vL + cL, vR + cR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        F[v] = (Real(0.5) * (FL[v] + FR[v]) - Real(0.5) * lam * (uR[v] - uL[v])) * area;
+}
+
+// Viscous flux F_vis (Eqs. 4, 6, 7 in the standard sign: [0, tau_ij, V_i tau_ij - q_j],
+// q_j = -(mu gamma / Pr) de/dx_j) from u and conserved-variable gradients G[v][j].
+template <int DIM, typename Real>
+__device__ __forceinline__ void visc_flux(const Real* u, const Real (*G)[DIM], Real mu, Real kappa,
+                                          Real (*F)[DIM]) {
+    constexpr int NV = DIM + 2;
+    const Real ir = Real(1) / u[0];
+    Real V[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) V[i] = u[1 + i] * ir;
+    Real gV[DIM][DIM];
+    Real ge[DIM];
+    const Real Er = u[NV - 1] * ir;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        Real s = (G[NV - 1][j] - Er * G[0][j]) * ir;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            gV[i][j] = (G[1 + i][j] - V[i] * G[0][j]) * ir;
+            s -= V[i] * gV[i][j];
+        }
+        ge[j] = s;
+    }
+    Real div = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) div += gV[i][i];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        F[0][j] = Real(0);
+        Real work = Real(0);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            Real t = mu * (gV[i][j] + gV[j][i]);
+            if (i == j) t -= Real(2.0 / 3.0) * mu * div;
+            F[1 + i][j] = t;
+            work += V[i] * t;
+        }
+        F[NV - 1][j] = work + kappa * ge[j];
+    }
+}
+
+// Boundary states: ghost for the inviscid flux and common solution u_b.
+template <int DIM, typename Real>
+__device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N, const Phys<Real>& ph,
+                                         Real* ug, Real* ub) {
+    constexpr int NV = DIM + 2;
+    Real a2 = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) a2 += N[i] * N[i];
+    const Real ia = Real(1) / sqrt(a2);
+    Real n[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) n[i] = N[i] * ia;
+    if (tag == FR_BC_WALL) {
+        if (ph.viscous) {
+            Real m2 = Real(0);
+            ug[0] = uL[0];
+            ub[0] = uL[0];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                ug[1 + i] = -uL[1 + i];
+                ub[1 + i] = Real(0);
+                m2 += uL[1 + i] * uL[1 + i];
+            }
+            ug[NV - 1] = uL[NV - 1];
+            ub[NV - 1] = uL[NV - 1] - Real(0.5) * m2 / uL[0];
+        } else {
+            Real mn = Real(0);
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) mn += uL[1 + i] * n[i];
+            ug[0] = uL[0];
+            ub[0] = uL[0];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                ug[1 + i] = uL[1 + i] - Real(2) * mn * n[i];
+                ub[1 + i] = uL[1 + i] - mn * n[i];
+            }
+            ug[NV - 1] = uL[NV - 1];
+            ub[NV - 1] = uL[NV - 1] - Real(0.5) * mn * mn / uL[0];
+        }
+        return;
+    }
+    // characteristic far field
+    const Real g = ph.gamma, gm1 = ph.gm1;
+    const Real rhoL = uL[0];
+    const Real pL = pressure<DIM>(uL, gm1);
+    const Real cL = sqrt(g * pL / rhoL);
+    Real vnL = Real(0), vnI = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        vnL += uL[1 + i] * n[i];
+        vnI += ph.vel_inf[i] * n[i];
+    }
+    vnL /= rhoL;
+    const Real cI = sqrt(g * ph.p_inf / ph.rho_inf);
+    if (fabs(vnI) >= cI) {
+        if (vnI < Real(0)) {
+            Real v2 = Real(0);
+            ub[0] = ph.rho_inf;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                ub[1 + i] = ph.rho_inf * ph.vel_inf[i];
+                v2 += ph.vel_inf[i] * ph.vel_inf[i];
+            }
+            ub[NV - 1] = ph.p_inf / gm1 + Real(0.5) * ph.rho_inf * v2;
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ub[v] = uL[v];
+        }
+    } else {
+        const Real Rp = vnL + Real(2) * cL / gm1;
+        const Real Rm = vnI - Real(2) * cI / gm1;
+        const Real vnb = Real(0.5) * (Rp + Rm);
+        const Real cb = Real(0.25) * gm1 * (Rp - Rm);
+        Real s, Vt[DIM];
+        if (vnb > Real(0)) {
+            s = pL / pow(rhoL, g);
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) Vt[i] = uL[1 + i] / rhoL - vnL * n[i];
+        } else {
+            s = ph.p_inf / pow(ph.rho_inf, g);
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) Vt[i] = ph.vel_inf[i] - vnI * n[i];
+        }
+        const Real rhob = pow(cb * cb / (g * s), Real(1) / gm1);
+        const Real pb = rhob * cb * cb / g;
+        Real v2 = Real(0);
+        ub[0] = rhob;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            const Real Vb = Vt[i] + vnb * n[i];
+            ub[1 + i] = rhob * Vb;
+            v2 += Vb * Vb;
+        }
+        ub[NV - 1] = pb / gm1 + Real(0.5) * rhob * v2;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ug[v] = ub[v];
+}
+
+template <typename Real>
+__device__ __forceinline__ void copy_ops(Ops<Real>* dst, const Ops<Real>* src) {
+    const Real* s = reinterpret_cast<const Real*>(src);
+    Real* d = reinterpret_cast<Real*>(dst);
+    constexpr int n = sizeof(Ops<Real>) / sizeof(Real);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = s[k];
+}
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// shared-memory footprint (bytes) of each kernel for epb elements
+template <int DIM, int P, typename Real>
+__host__ __device__ constexpr size_t smem_traces(int epb) {
+    using Z = Sz<DIM, P>;
+    return align_up(sizeof(Ops<Real>), 16) + sizeof(Real) * size_t(epb) * Z::NV * Z::NSP;
+}
+template <int DIM, int P, typename Real>
+__host__ __device__ constexpr size_t smem_visc(int epb) {
+    using Z = Sz<DIM, P>;
+    return align_up(sizeof(Ops<Real>), 16) +
+           sizeof(Real) * size_t(epb) * (Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + Z::NV * DIM * Z::NSP);
+}
+template <int DIM, int P, typename Real>
+__host__ __device__ constexpr size_t smem_resid(int epb) {
+    using Z = Sz<DIM, P>;
+    return align_up(sizeof(Ops<Real>), 16) +
+           sizeof(Real) * size_t(epb) * (Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP);
+}
+
+// ---------------------------------------------------------------- kernels
+// Sweep A: traces of the solution at all flux points.
+template <int DIM, int P, typename Real>
+__global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int64_t E, int epb,
+                         const Ops<Real>* __restrict__ opg) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
+    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
+    const int64_t e0 = int64_t(blockIdx.x) * epb;
+    const int ne = int(min(int64_t(epb), E - e0));
+    copy_ops(op, opg);
+    const Real* ug = u + e0 * NV * NSP;
+    for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
+    __syncthreads();
+    Real* ufg = uf + e0 * NF * NV * NFP;
+    for (int w = threadIdx.x; w < ne * NF * NV * NFP; w += blockDim.x) {
+        const int fp = w % NFP;
+        int t = w / NFP;
+        const int v = t % NV;
+        t /= NV;
+        const int f = t % NF;
+        const int el = t / NF;
+        const int d = f >> 1;
+        const Real* l = (f & 1) ? op->lp : op->lm;
+        const Real* s = su + (el * NV + v) * NSP;
+        Real acc = Real(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
+        ufg[w] = acc;
+    }
+}
+
+template <int DIM, typename Real>
+__device__ __forceinline__ void load_normal(const Geo<Real>& g, int64_t e, int f, int fp, Real* N) {
+    const Real* p = g.N + (e * (2 * DIM) + f) * g.sN_f + fp * g.sN_fp;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) N[i] = p[i];
+}
+
+// Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
+// boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
+// an adiabatic wall) is written instead.
+template <int DIM, int P, typename Real>
+__global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
+                            int64_t E, int epb, const Ops<Real>* __restrict__ opg, Phys<Real> ph, Geo<Real> g) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
+    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
+    Real* sj = su + epb * NV * NSP;           // jumps u_c - u_f   [el][f][v][fp]
+    Real* sl = sj + epb * NF * NV * NFP;      // own traces u_f    [el][f][v][fp]
+    Real* sg = sl + epb * NF * NV * NFP;      // grad_D u          [el][v][i][sp]
+    const int64_t e0 = int64_t(blockIdx.x) * epb;
+    const int ne = int(min(int64_t(epb), E - e0));
+    copy_ops(op, opg);
+    {
+        const Real* ug = u + e0 * NV * NSP;
+        for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
+    }
+    __syncthreads();
+    // P1: traces, neighbour traces, jumps
+    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
+        const int fp = w % NFP;
+        const int f = (w / NFP) % NF;
+        const int el = w / (NFP * NF);
+        const int d = f >> 1;
+        const Real* l = (f & 1) ? op->lp : op->lm;
+        Real uL[NV], uc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const Real* s = su + (el * NV + v) * NSP;
+            Real acc = Real(0);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
+            uL[v] = acc;
+        }
+        const int code = g.nbr[(e0 + el) * NF + f];
+        if (code >= 0) {
+            const Real* un = uf + int64_t(code >> 3) * NV * NFP;
+            const int fpn = omap<DIM, NP>(code & 7, fp);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) uc[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]);
+        } else {
+            Real N[DIM], ug[NV];
+            load_normal<DIM>(g, e0 + el, f, fp, N);
+            bc_state<DIM>(-code, uL, N, ph, ug, uc);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            sj[((el * NF + f) * NV + v) * NFP + fp] = uc[v] - uL[v];
+            sl[((el * NF + f) * NV + v) * NFP + fp] = uL[v];
+        }
+    }
+    // P2: uncorrected physical gradient at solution points
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int sp = w % NSP;
+        const int el = w / NSP;
+        const int64_t e = e0 + el;
+        Real q[DIM][NV];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            int fpd, jd;
+            sp_split<DIM, NP>(sp, d, fpd, jd);
+            const Real* Drow = op->D + jd * MAXNP;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const Real* s = su + (el * NV + v) * NSP;
+                Real acc = Real(0);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) acc += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
+                q[d][v] = acc;
+            }
+        }
+        Real S[DIM * DIM];
+#pragma unroll
+        for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
+        const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                Real acc = Real(0);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
+                sg[((el * NV + v) * DIM + i) * NSP + sp] = acc * iJ;
+            }
+    }
+    __syncthreads();
+    // P3: lifted face gradient and viscous normal flux
+    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
+        const int fp = w % NFP;
+        const int f = (w / NFP) % NF;
+        const int el = w / (NFP * NF);
+        const int64_t e = e0 + el;
+        const int d = f >> 1;
+        const bool side = (f & 1) != 0;
+        const Real* l = side ? op->lp : op->lm;
+        const Real* h = side ? op->hp : op->hm;
+        const Real nsg = side ? Real(1) : Real(-1);
+        // lifting coefficient along the line: sum_j l_j h_j S_j[d][i] / J_j
+        Real lc[DIM];
+        if (g.sS_sp == 0 && g.sJ_sp == 0) {
+            const Real lh = side ? op->lhp : op->lhm;
+            const Real iJ = Real(1) / g.J[e * g.sJ_e];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) lc[i] = nsg * lh * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
+        } else {
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) lc[i] = Real(0);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const int sp = line_sp<DIM, NP>(d, fp, j);
+                const Real c = l[j] * h[j] / g.J[e * g.sJ_e + sp * g.sJ_sp];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) lc[i] += c * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k + sp * g.sS_sp];
+            }
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
+        }
+        Real G[NV][DIM];
+        Real uL[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const Real jv = sj[((el * NF + f) * NV + v) * NFP + fp];
+            uL[v] = sl[((el * NF + f) * NV + v) * NFP + fp];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                const Real* s = sg + ((el * NV + v) * DIM + i) * NSP;
+                Real acc = Real(0);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
+                G[v][i] = acc + ph.eta * lc[i] * jv;
+            }
+        }
+        Real N[DIM];
+        load_normal<DIM>(g, e, f, fp, N);
+        const int code = g.nbr[e * NF + f];
+        Real Fv[NV][DIM];
+        Real out[NV];
+        if (code >= 0) {
+            visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
+        } else {
+            Real ug[NV], ub[NV];
+            bc_state<DIM>(-code, uL, N, ph, ug, ub);
+            visc_flux<DIM>(ub, G, ph.mu, ph.kappa, Fv);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) acc += Fv[v][i] * N[i];
+            out[v] = acc;
+        }
+        if (code == -FR_BC_WALL) out[NV - 1] = Real(0);
+        Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[v * NFP] = out[v];
+    }
+}
+
+// Sweep C: common fluxes, corrected gradient, flux divergence with FR
+// correction, residual R = -(1/|J|)[...], fused with the RK4 stage update.
+template <int DIM, int P, typename Real>
+__global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
+                           const Real* __restrict__ fvn, int64_t E, int epb,
+                           const Ops<Real>* __restrict__ opg, Phys<Real> ph, Geo<Real> g, Stage<Real> st) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
+    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
+    Real* sj = su + epb * NV * NSP;           // jumps            [el][f][v][fp]
+    Real* sc = sj + epb * NF * NV * NFP;      // Fc.N - own F~.n  [el][f][v][fp]
+    Real* sF = sc + epb * NF * NV * NFP;      // F~_d             [el][d][v][sp]
+    const int64_t e0 = int64_t(blockIdx.x) * epb;
+    const int ne = int(min(int64_t(epb), E - e0));
+    copy_ops(op, opg);
+    {
+        const Real* ug = u + e0 * NV * NSP;
+        for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
+    }
+    __syncthreads();
+    // P1: common normal flux (inviscid Rusanov minus common viscous) and jumps
+    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
+        const int fp = w % NFP;
+        const int f = (w / NFP) % NF;
+        const int el = w / (NFP * NF);
+        const int64_t e = e0 + el;
+        const int d = f >> 1;
+        const Real* l = (f & 1) ? op->lp : op->lm;
+        Real uL[NV], uR[NV], uc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const Real* s = su + (el * NV + v) * NSP;
+            Real acc = Real(0);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
+            uL[v] = acc;
+        }
+        Real N[DIM];
+        load_normal<DIM>(g, e, f, fp, N);
+        const int code = g.nbr[e * NF + f];
+        int64_t nslot = 0;
+        int fpn = 0;
+        if (code >= 0) {
+            nslot = int64_t(code >> 3);
+            fpn = omap<DIM, NP>(code & 7, fp);
+            const Real* un = uf + nslot * NV * NFP;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                uR[v] = un[v * NFP + fpn];
+                uc[v] = Real(0.5) * (uL[v] + uR[v]);
+            }
+        } else {
+            bc_state<DIM>(-code, uL, N, ph, uR, uc);
+        }
+        Real Fc[NV];
+        rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
+        if (ph.viscous) {
+            const Real* own = fvn + (e * NF + f) * NV * NFP + fp;
+            if (code >= 0) {
+                const Real* nb = fvn + nslot * NV * NFP + fpn;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Fc[v] -= Real(0.5) * (own[v * NFP] - nb[v * NFP]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Fc[v] -= own[v * NFP];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            sj[((el * NF + f) * NV + v) * NFP + fp] = uc[v] - uL[v];
+            sc[((el * NF + f) * NV + v) * NFP + fp] = Fc[v];
+        }
+    }
+    __syncthreads();
+    // P2: flux at solution points, transformed: F~_d = sum_i S[d][i] (F_inv - F_vis)_i
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int sp = w % NSP;
+        const int el = w / NSP;
+        const int64_t e = e0 + el;
+        Real uu[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uu[v] = su[(el * NV + v) * NSP + sp];
+        Real S[DIM * DIM];
+#pragma unroll
+        for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
+        Real F[NV][DIM];
+        const Real p = pressure<DIM>(uu, ph.gm1);
+        {
+            const Real ir = Real(1) / uu[0];
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+                const Real vj = uu[1 + j] * ir;
+                F[0][j] = uu[1 + j];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) F[1 + i][j] = uu[1 + i] * vj + (i == j ? p : Real(0));
+                F[NV - 1][j] = (uu[NV - 1] + p) * vj;
+            }
+        }
+        if (ph.viscous) {
+            Real q[DIM][NV];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                int fpd, jd;
+                sp_split<DIM, NP>(sp, d, fpd, jd);
+                const Real* Drow = op->D + jd * MAXNP;
+                const Real hmv = -op->hm[jd];
+                const Real hpv = op->hp[jd];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const Real* s = su + (el * NV + v) * NSP;
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) acc += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
+                    acc += hmv * sj[((el * NF + 2 * d) * NV + v) * NFP + fpd];
+                    acc += hpv * sj[((el * NF + 2 * d + 1) * NV + v) * NFP + fpd];
+                    q[d][v] = acc;
+                }
+            }
+            const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
+            Real G[NV][DIM];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) {
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
+                    G[v][i] = acc * iJ;
+                }
+            Real Fv[NV][DIM];
+            visc_flux<DIM>(uu, G, ph.mu, ph.kappa, Fv);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) F[v][i] -= Fv[v][i];
+        }
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Real acc = Real(0);
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];
+                sF[((el * DIM + d) * NV + v) * NSP + sp] = acc;
+            }
+    }
+    __syncthreads();
+    // P3: flux jump at flux points: Fc.N - nsign I_f[F~_d]
+    for (int w = threadIdx.x; w < ne * NF * NV * NFP; w += blockDim.x) {
+        const int fp = w % NFP;
+        int t = w / NFP;
+        const int v = t % NV;
+        t /= NV;
+        const int f = t % NF;
+        const int el = t / NF;
+        const int d = f >> 1;
+        const bool side = (f & 1) != 0;
+        const Real* l = side ? op->lp : op->lm;
+        const Real* s = sF + ((el * DIM + d) * NV + v) * NSP;
+        Real acc = Real(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
+        Real* c = sc + ((el * NF + f) * NV + v) * NFP + fp;
+        *c = side ? (*c - acc) : (*c + acc);
+    }
+    __syncthreads();
+    // P4: divergence + correction, residual, RK stage
+    for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) {
+        const int sp = w % NSP;
+        const int v = (w / NSP) % NV;
+        const int el = w / (NSP * NV);
+        const int64_t e = e0 + el;
+        Real div = Real(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            int fpd, jd;
+            sp_split<DIM, NP>(sp, d, fpd, jd);
+            const Real* Drow = op->D + jd * MAXNP;
+            const Real* s = sF + ((el * DIM + d) * NV + v) * NSP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) div += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
+            div += op->hm[jd] * sc[((el * NF + 2 * d) * NV + v) * NFP + fpd];
+            div += op->hp[jd] * sc[((el * NF + 2 * d + 1) * NV + v) * NFP + fpd];
+        }
+        const Real r = -div / g.J[e * g.sJ_e + sp * g.sJ_sp];
+        const int64_t gi = e0 * NV * NSP + w;
+        switch (st.stage) {
+            case 0:
+                st.R[gi] = r;
+                break;
+            case 1:
+                st.acc[gi] = (st.dt * Real(1.0 / 6.0)) * r;
+                st.us[gi] = su[w] + (st.dt * Real(0.5)) * r;
+                break;
+            case 2:
+                st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
+                st.us[gi] = st.u0[gi] + (st.dt * Real(0.5)) * r;
+                break;
+            case 3:
+                st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
+                st.us[gi] = st.u0[gi] + st.dt * r;
+                break;
+            default:
+                st.u0[gi] = st.u0[gi] + st.acc[gi] + (st.dt * Real(1.0 / 6.0)) * r;
+                break;
+        }
+    }
+}
+
+// Wall force (Section 3.2): one block per candidate sums, over that
+// candidate's wall face points, w_fp (p N - tau.N) with N the element's
+// outward area-weighted normal (into the body), p from the interior trace and
+// tau.N the momentum entries of the wall's common viscous flux.  Accumulated
+// in double; fnow/fsum/fcnt are updated in place (graph-replay safe).
+template <int DIM, int P, typename Real>
+__global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ fvn,
+                         const int32_t* __restrict__ wall_ef, const int64_t* __restrict__ wall_off,
+                         const Ops<Real>* __restrict__ op, Geo<Real> g, Real gm1, int viscous,
+                         double* __restrict__ fnow, double* __restrict__ fsum, double* __restrict__ fcnt) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    __shared__ double red[DIM][256];
+    const int c = blockIdx.x;
+    const int64_t b = wall_off[c], n = wall_off[c + 1] - b;
+    double acc[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) acc[i] = 0.0;
+    for (int64_t w = threadIdx.x; w < n * NFP; w += blockDim.x) {
+        const int fp = int(w % NFP);
+        const int32_t ef = wall_ef[b + w / NFP];
+        const int64_t e = ef / NF;
+        const int f = ef % NF;
+        Real uL[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uL[v] = uf[int64_t(ef) * NV * NFP + v * NFP + fp];
+        const Real p = pressure<DIM>(uL, gm1);
+        Real N[DIM];
+        load_normal<DIM>(g, e, f, fp, N);
+        const double wt = (DIM == 2) ? double(op->w[fp]) : double(op->w[fp % NP]) * double(op->w[fp / NP]);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            double fi = double(p) * double(N[i]);
+            if (viscous) fi -= double(fvn[int64_t(ef) * NV * NFP + (1 + i) * NFP + fp]);
+            acc[i] += wt * fi;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) red[i][threadIdx.x] = acc[i];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            fnow[c * 3 + i] = red[i][0];
+            fsum[c * 3 + i] += red[i][0];
+        }
+        fcnt[c] += 1.0;
+    }
+}
+
+// FW-H data-surface sampling (Section 3.1): one warp per surface point
+// evaluates the element's tensor Lagrange interpolant (1D weights pw
+// [npts][DIM][NP] precomputed at the located reference coordinates) and
+// stores (rho, V_1, V_2, V_3, p) minus the free stream into record *count.
+template <int DIM, int P, typename Real>
+__global__ void k_sample(const Real* __restrict__ u, const int64_t* __restrict__ pe,
+                         const Real* __restrict__ pw, int npts, Phys<Real> ph, Real* __restrict__ hist,
+                         const int* __restrict__ count, int cap) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NSP = Z::NSP, NV = Z::NV;
+    const int lane = threadIdx.x & 31;
+    const int k = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (k >= npts) return;
+    const int rec = *count;
+    if (rec >= cap) return;
+    const Real* ue = u + pe[k] * NV * NSP;
+    const Real* wk = pw + int64_t(k) * DIM * NP;
+    Real acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = Real(0);
+    for (int sp = lane; sp < NSP; sp += 32) {
+        Real wt = wk[sp % NP];
+        wt *= wk[NP + (sp / NP) % NP];
+        if (DIM == 3) wt *= wk[2 * NP + sp / (NP * NP)];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += wt * ue[v * NSP + sp];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    if (lane == 0) {
+        const Real rho = acc[0];
+        const Real p = pressure<DIM>(acc, ph.gm1);
+        Real* dst = hist + (int64_t(rec) * npts + k) * 5;
+        dst[0] = rho - ph.rho_inf;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dst[1 + i] = (i < DIM) ? acc[1 + i] / rho - ph.vel_inf[i] : Real(0);
+        dst[4] = p - ph.p_inf;
+    }
+}
+
+// advances a record counter after the sampling kernel of the same step
+static __global__ void k_bump(int* count, int cap, int* overflow) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (*count < cap) *count += 1;
+        else *overflow = 1;
+    }
+}
+
+// Volume integrals (double) of the conserved variables and of the kinetic
+// energy over elements [e_first, e_first + ne): one partial row per block.
+template <int DIM, int P, typename Real>
+__global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t ne,
+                            const Ops<Real>* __restrict__ op, Geo<Real> g, double* __restrict__ partial) {
+    using Z = Sz<DIM, P>;
+    constexpr int NP = Z::NP, NSP = Z::NSP, NV = Z::NV;
+    __shared__ double red[NV + 1][256];
+    double acc[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < ne * NSP;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t e = e_first + w / NSP;
+        const int sp = int(w % NSP);
+        double wt = double(op->w[sp % NP]) * double(op->w[(sp / NP) % NP]);
+        if (DIM == 3) wt *= double(op->w[sp / (NP * NP)]);
+        wt *= double(g.J[e * g.sJ_e + sp * g.sJ_sp]);
+        const Real* ue = u + e * NV * NSP + sp;
+        double m2 = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double x = double(ue[v * NSP]);
+            acc[v] += wt * x;
+            if (v >= 1 && v <= DIM) m2 += x * x;
+        }
+        acc[NV] += wt * 0.5 * m2 / double(ue[0]);
+    }
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int v = 0; v <= NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int v = 0; v <= NV; ++v) partial[blockIdx.x * (NV + 1) + v] = red[v][0];
+}
+
+}  // namespace frk

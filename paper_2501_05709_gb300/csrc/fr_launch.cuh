@@ -1,0 +1,157 @@
+// Host launchers of the FR kernels for one (precision, dimension) pair; the
+// including translation unit defines FR_REAL and FR_DIM.
+#include "fr_kernels.cuh"
+
+namespace frl {
+
+namespace {
+
+// Opt every kernel in to the full 227 KB of dynamic shared memory on its first
+// use (a launch with E == 0 does only this), so that later launches of any
+// tile size, including those recorded into a CUDA graph, need no attribute call.
+template <typename K>
+cudaError_t prep(K kernel, size_t smem) {
+    static bool done = false;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+inline unsigned grid_of(int64_t E, int epb) { return unsigned((E + epb - 1) / epb); }
+
+template <int P>
+int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* op, frk::Launch lc,
+             cudaStream_t s) {
+    auto k = frk::k_traces<FR_DIM, P, FR_REAL>;
+    const size_t sm = frk::smem_traces<FR_DIM, P, FR_REAL>(lc.epb);
+    cudaError_t e = prep(k, sm);
+    if (e != cudaSuccess) return int(e);
+    if (E == 0) return 0;
+    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, E, lc.epb, op);
+    return int(cudaGetLastError());
+}
+
+template <int P>
+int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>* op,
+           const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
+    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL>;
+    const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb);
+    cudaError_t e = prep(k, sm);
+    if (e != cudaSuccess) return int(e);
+    if (E == 0) return 0;
+    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g);
+    return int(cudaGetLastError());
+}
+
+template <int P>
+int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
+            const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
+            const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
+    auto k = frk::k_residual<FR_DIM, P, FR_REAL>;
+    const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb);
+    cudaError_t e = prep(k, sm);
+    if (e != cudaSuccess) return int(e);
+    if (E == 0) return 0;
+    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g, st);
+    return int(cudaGetLastError());
+}
+
+}  // namespace
+
+#define FR_DISPATCH(CALL)                 \
+    switch (P) {                          \
+        case 1: return CALL(1);           \
+        case 2: return CALL(2);           \
+        case 3: return CALL(3);           \
+        case 4: return CALL(4);           \
+        default: return int(cudaErrorInvalidValue); \
+    }
+
+template <>
+int traces<FR_REAL, FR_DIM>(int P, const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* op,
+                            frk::Launch lc, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define C(PP) traces_p<PP>(u, uf, E, op, lc, s)
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
+int visc_face<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E,
+                               const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph,
+                               const frk::Geo<FR_REAL>& g, frk::Launch lc, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define C(PP) visc_p<PP>(u, uf, fvn, E, op, ph, g, lc, s)
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
+int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
+                              const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph,
+                              const frk::Geo<FR_REAL>& g, const frk::Stage<FR_REAL>& st, frk::Launch lc,
+                              void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define C(PP) resid_p<PP>(u, uf, fvn, E, op, ph, g, st, lc, s)
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
+size_t smem_bytes<FR_REAL, FR_DIM>(int P, int kernel, int epb) {
+#define C(PP) (kernel == 0 ? frk::smem_traces<FR_DIM, PP, FR_REAL>(epb) \
+               : kernel == 1 ? frk::smem_visc<FR_DIM, PP, FR_REAL>(epb)  \
+                             : frk::smem_resid<FR_DIM, PP, FR_REAL>(epb))
+    switch (P) {
+        case 1: return C(1);
+        case 2: return C(2);
+        case 3: return C(3);
+        case 4: return C(4);
+        default: return 0;
+    }
+#undef C
+}
+
+template <>
+int forces<FR_REAL, FR_DIM>(int P, const FR_REAL* uf, const FR_REAL* fvn, const int32_t* wall_ef,
+                            const int64_t* wall_off, int ncand, const frk::Ops<FR_REAL>* op,
+                            const frk::Geo<FR_REAL>& g, FR_REAL gm1, int viscous, double* fnow, double* fsum,
+                            double* fcnt, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ncand <= 0) return 0;
+#define C(PP) (frk::k_forces<FR_DIM, PP, FR_REAL><<<ncand, 256, 0, s>>>(uf, fvn, wall_ef, wall_off, op, g, gm1, \
+                                                                         viscous, fnow, fsum, fcnt),         \
+               int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
+int sample<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const int64_t* pe, const FR_REAL* pw, int npts,
+                            const frk::Phys<FR_REAL>& ph, FR_REAL* hist, int* count, int cap, int* overflow,
+                            void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned blocks = unsigned((int64_t(npts) * 32 + 255) / 256);
+#define C(PP) ((npts > 0 ? (frk::k_sample<FR_DIM, PP, FR_REAL><<<blocks, 256, 0, s>>>(u, pe, pw, npts, ph, hist, \
+                                                                                  count, cap), 0) : 0),        \
+               frk::k_bump<<<1, 32, 0, s>>>(count, cap, overflow), int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
+int integrals<FR_REAL, FR_DIM>(int P, const FR_REAL* u, int64_t e_first, int64_t ne,
+                               const frk::Ops<FR_REAL>* op, const frk::Geo<FR_REAL>& g, double* partial,
+                               int nblocks, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+#define C(PP) (frk::k_integrals<FR_DIM, PP, FR_REAL><<<nblocks, 256, 0, s>>>(u, e_first, ne, op, g, partial), \
+               int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
+#undef FR_DISPATCH
+
+}  // namespace frl

@@ -1,0 +1,266 @@
+// FW-H acoustic pressure at far-field observers from a stationary permeable
+// data surface in a uniformly moving medium (Appendix B, Eqs. B.2-B.14),
+// advanced-time (source-time-dominant) form, in double precision.
+//
+//   k_fwh_series : per panel and source time, the thickness and loading
+//                  sources Q (Eq. A.5) and L_i (Eqs. A.7-A.8, sigma_ij
+//                  omitted), with u_i the disturbance velocity V - U_inf,
+//                  and their 4th-order finite-difference tau-derivatives.
+//   k_fwh_accum  : per (panel, spanwise copy) the radii R*, R and their
+//                  gradients (Eqs. B.8-B.12) give the integrand coefficients
+//                  of Eqs. B.2-B.3; each observer time t* (unified window,
+//                  step dtau) interpolates the panel integrand at
+//                  tau = t* - R/c0 (Eq. B.13) with a 4-point cubic Lagrange
+//                  stencil and sums (Eq. B.14); one partial row per panel group.
+//   k_fwh_reduce : sums the partial rows in a fixed order, divides by 4 pi.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "fr.h"
+
+namespace {
+
+constexpr int NSER = 8;  // Q, L1, L2, L3, dQ, dL1, dL2, dL3
+
+struct FwhConst {
+    double M[3];
+    double c0, rho0, p0, dtau, tau0;
+    double b2;  // Prandtl-Glauert factor squared, 1 / (1 - |M|^2)
+};
+
+__device__ __forceinline__ void sources(const double* h, const double* n, const FwhConst& k, double* out) {
+    // h = (rho, V1, V2, V3, p) total; disturbance u = V - c0 M
+    double u[3];
+    double un = 0.0, Un = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        u[i] = h[1 + i] - k.c0 * k.M[i];
+        un += u[i] * n[i];
+        Un += k.c0 * k.M[i] * n[i];
+    }
+    const double rho = h[0];
+    out[0] = rho * (un + Un) - k.rho0 * Un;
+    for (int i = 0; i < 3; ++i) out[1 + i] = (h[4] - k.p0) * n[i] + rho * u[i] * (un + Un);
+}
+
+__global__ void k_fwh_series(const double* __restrict__ hist, int nt, int npts, const double* __restrict__ nrm,
+                             FwhConst k, double* __restrict__ X) {
+    const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (w >= int64_t(nt) * npts) return;
+    const int p = int(w % npts);
+    const int t = int(w / npts);
+    const double n[3] = {nrm[p * 3 + 0], nrm[p * 3 + 1], nrm[p * 3 + 2]};
+    // the 5-point stencil: central inside, one-sided 4th order at both ends
+    int j0;
+    double c[5];
+    const double s = 1.0 / (12.0 * k.dtau);
+    if (t >= 2 && t <= nt - 3) {
+        j0 = t - 2;
+        c[0] = 1; c[1] = -8; c[2] = 0; c[3] = 8; c[4] = -1;
+    } else if (t == 0) {
+        j0 = 0;
+        c[0] = -25; c[1] = 48; c[2] = -36; c[3] = 16; c[4] = -3;
+    } else if (t == 1) {
+        j0 = 0;
+        c[0] = -3; c[1] = -10; c[2] = 18; c[3] = -6; c[4] = 1;
+    } else if (t == nt - 1) {
+        j0 = nt - 5;
+        c[0] = 3; c[1] = -16; c[2] = 36; c[3] = -48; c[4] = 25;
+    } else {
+        j0 = nt - 5;
+        c[0] = -1; c[1] = 6; c[2] = -18; c[3] = 10; c[4] = 3;
+    }
+    double here[4], der[4] = {0, 0, 0, 0};
+    sources(hist + (int64_t(t) * npts + p) * 5, n, k, here);
+    for (int m = 0; m < 5; ++m) {
+        double q[4];
+        sources(hist + (int64_t(j0 + m) * npts + p) * 5, n, k, q);
+        for (int v = 0; v < 4; ++v) der[v] += c[m] * q[v];
+    }
+    double* xp = X + int64_t(p) * NSER * nt;
+    for (int v = 0; v < 4; ++v) {
+        xp[v * nt + t] = here[v];
+        xp[(4 + v) * nt + t] = der[v] * s;
+    }
+}
+
+// Geometry of one (panel, copy): integrand coefficients and delay.
+__device__ void panel_coefs(const double* y, double dS, const double* obs, const FwhConst& k, double* cf,
+                            double* delay) {
+    double r[3];
+    for (int i = 0; i < 3; ++i) r[i] = obs[i] - y[i];
+    double Mr = 0, rr = 0, MM = 0;
+    for (int i = 0; i < 3; ++i) {
+        Mr += k.M[i] * r[i];
+        rr += r[i] * r[i];
+        MM += k.M[i] * k.M[i];
+    }
+    (void)MM;
+    const double b2 = k.b2;
+    const double Rs = sqrt(rr + b2 * Mr * Mr) / sqrt(b2);          // Eq. B.8
+    const double R = b2 * (Rs - Mr);                               // Eq. B.9
+    double Rts[3], Rt[3];
+    double MRs = 0, MR = 0;
+    for (int i = 0; i < 3; ++i) {
+        Rts[i] = (r[i] + b2 * Mr * k.M[i]) / (b2 * Rs);            // Eq. B.11
+        Rt[i] = b2 * (Rts[i] - k.M[i]);                            // Eq. B.12
+        MRs += k.M[i] * Rts[i];
+        MR += k.M[i] * Rt[i];
+    }
+    // I = a dQ + b Q + sum_i (d_i dL_i + e_i L_i)   (Eqs. B.2-B.7, times dS)
+    cf[4] = (1.0 - MR) * dS / Rs;
+    cf[0] = -k.c0 * MRs * dS / (Rs * Rs);
+    for (int i = 0; i < 3; ++i) {
+        cf[5 + i] = Rt[i] * dS / (k.c0 * Rs);
+        cf[1 + i] = Rts[i] * dS / (Rs * Rs);
+    }
+    *delay = R / k.c0;
+}
+
+__global__ void k_fwh_accum(const double* __restrict__ X, int nt, int npts, const double* __restrict__ y,
+                            const double* __restrict__ dS, FwhConst k, double ox, double oy, double oz,
+                            double tstart, int T, int ncopies, double Lspan, int group,
+                            double* __restrict__ partial) {
+    extern __shared__ double sh[];  // [group*ncopies][NSER + 1]
+    const int p0 = blockIdx.y * group;
+    const int np = min(group, npts - p0);
+    const int npc = np * ncopies;
+    const int K = (ncopies - 1) / 2;
+    const double obs[3] = {ox, oy, oz};
+    for (int w = threadIdx.x; w < npc; w += blockDim.x) {
+        const int p = p0 + w / ncopies;
+        const int cc = w % ncopies - K;
+        const double yy[3] = {y[p * 3 + 0], y[p * 3 + 1], y[p * 3 + 2] + cc * Lspan};
+        double delay;
+        panel_coefs(yy, dS[p], obs, k, sh + w * (NSER + 1), &delay);
+        sh[w * (NSER + 1) + NSER] = (tstart - k.tau0 - delay) / k.dtau;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    double acc = 0.0;
+    for (int w = 0; w < npc; ++w) {
+        const double* cf = sh + w * (NSER + 1);
+        const double s = double(i) + cf[NSER];
+        int j0 = int(floor(s)) - 1;
+        j0 = max(0, min(nt - 4, j0));
+        const double x = s - double(j0);
+        // cubic Lagrange weights on nodes 0..3 at x
+        const double w0 = -(x - 1.0) * (x - 2.0) * (x - 3.0) / 6.0;
+        const double w1 = x * (x - 2.0) * (x - 3.0) / 2.0;
+        const double w2 = -x * (x - 1.0) * (x - 3.0) / 2.0;
+        const double w3 = x * (x - 1.0) * (x - 2.0) / 6.0;
+        const double wt[4] = {w0, w1, w2, w3};
+        const double* xp = X + int64_t(p0 + w / ncopies) * NSER * nt + j0;
+        double sum = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            double Ik = 0.0;
+#pragma unroll
+            for (int v = 0; v < NSER; ++v) Ik += cf[v] * xp[v * nt + m];
+            sum += wt[m] * Ik;
+        }
+        acc += sum;
+    }
+    partial[int64_t(blockIdx.y) * T + i] = acc;
+}
+
+__global__ void k_fwh_reduce(const double* __restrict__ partial, int ngroups, int T, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    double s = 0.0;
+    for (int g = 0; g < ngroups; ++g) s += partial[int64_t(g) * T + i];
+    out[i] = s / (4.0 * M_PI);
+}
+
+}  // namespace
+
+// records the message returned by fr_last_error (defined with the context code)
+int fr_set_error_from_fwh(int code, const char* msg);
+
+extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double* y, const double* n,
+                             const double* dS, double dtau, double tau0, const double* obs, int nobs,
+                             const double Minf[3], double c0, double rho0, double p0, double Lspan,
+                             int ncopies, double* p_out, int cap, int* nt_out, double* t0_out, void* stream) {
+    if (!hist || !y || !n || !dS || !obs || !Minf || !p_out || !nt_out || !t0_out)
+        return fr_set_error_from_fwh(FR_EINVAL, "null argument");
+    if (nt < 5 || npts < 1 || nobs < 1 || cap < 1 || ncopies < 1 || ncopies % 2 == 0 || !(dtau > 0.0) ||
+        !(c0 > 0.0))
+        return fr_set_error_from_fwh(FR_EINVAL, "bad sizes (nt >= 5, odd ncopies, dtau > 0, c0 > 0 required)");
+    const double MM = Minf[0] * Minf[0] + Minf[1] * Minf[1] + Minf[2] * Minf[2];
+    if (!(MM < 1.0)) return fr_set_error_from_fwh(FR_EINVAL, "|Minf| must be below 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FwhConst k;
+    for (int i = 0; i < 3; ++i) k.M[i] = Minf[i];
+    k.c0 = c0;
+    k.rho0 = rho0;
+    k.p0 = p0;
+    k.dtau = dtau;
+    k.tau0 = tau0;
+    k.b2 = 1.0 / (1.0 - MM);
+    // unified observer windows (host, double): needs panel positions
+    std::vector<double> yh(size_t(npts) * 3);
+    if (cudaMemcpyAsync(yh.data(), y, yh.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fr_set_error_from_fwh(FR_ECUDA, "cannot read panel positions");
+    const int K = (ncopies - 1) / 2;
+    std::vector<double> tstart(nobs);
+    std::vector<int> Tn(nobs);
+    for (int o = 0; o < nobs; ++o) {
+        double dmax = -1e300, dmin = 1e300;
+        for (int p = 0; p < npts; ++p)
+            for (int cc = -K; cc <= K; ++cc) {
+                double r[3] = {obs[o * 3 + 0] - yh[p * 3 + 0], obs[o * 3 + 1] - yh[p * 3 + 1],
+                               obs[o * 3 + 2] - (yh[p * 3 + 2] + cc * Lspan)};
+                double Mr = 0, rr = 0;
+                for (int i = 0; i < 3; ++i) {
+                    Mr += Minf[i] * r[i];
+                    rr += r[i] * r[i];
+                }
+                const double Rs = std::sqrt(rr + k.b2 * Mr * Mr) / std::sqrt(k.b2);
+                const double d = k.b2 * (Rs - Mr) / c0;
+                dmax = std::max(dmax, d);
+                dmin = std::min(dmin, d);
+            }
+        const double ts = tau0 + dmax;
+        const double te = tau0 + (nt - 1) * dtau + dmin;
+        if (te < ts) return fr_set_error_from_fwh(FR_EWINDOW, "empty observer window");
+        const int T = int(std::floor((te - ts) / dtau + 1e-9)) + 1;
+        if (T > cap) return fr_set_error_from_fwh(FR_EWINDOW, "observer window longer than the output capacity");
+        tstart[o] = ts;
+        Tn[o] = T;
+    }
+    const int group = std::max(1, 1024 / ncopies);
+    const int ngroups = (npts + group - 1) / group;
+    if (ngroups > 65535) return fr_set_error_from_fwh(FR_EINVAL, "too many panels for one launch");
+    int Tmax = *std::max_element(Tn.begin(), Tn.end());
+    double *X = nullptr, *partial = nullptr;
+    if (cudaMalloc(&X, sizeof(double) * size_t(npts) * NSER * nt) != cudaSuccess ||
+        cudaMalloc(&partial, sizeof(double) * size_t(ngroups) * Tmax) != cudaSuccess) {
+        if (X) cudaFree(X);
+        return fr_set_error_from_fwh(FR_ENOMEM, "cannot allocate FW-H scratch");
+    }
+    const int64_t nw = int64_t(nt) * npts;
+    k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
+    const size_t sm = sizeof(double) * size_t(group) * ncopies * (NSER + 1);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && sm > 48 * 1024)
+        err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
+        dim3 grid(unsigned((Tn[o] + 255) / 256), unsigned(ngroups));
+        k_fwh_accum<<<grid, 256, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
+                                          tstart[o], Tn[o], ncopies, Lspan, group, partial);
+        k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
+        err = cudaGetLastError();
+        nt_out[o] = Tn[o];
+        t0_out[o] = tstart[o];
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    cudaFree(X);
+    cudaFree(partial);
+    if (err != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, cudaGetErrorString(err));
+    return FR_OK;
+}

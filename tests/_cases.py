@@ -1,0 +1,87 @@
+"""Seeded parity cases shared by the GPU tests: a mesh from the workload
+generators, physics constants, and a state evaluated at the solution points."""
+import math
+
+import numpy as np
+
+from paper_2501_05709_gb300 import workloads as W
+
+GAMMA = 1.4
+
+
+def _conserved_at(xsp, fn, **kw):
+    return np.ascontiguousarray(np.moveaxis(fn(xsp, **kw), 0, 1))
+
+
+def make_case(name):
+    """Returns dict(nodes, conn, p, kind, mu, visc, freestream, state(xsp) -> u, dt)."""
+    c = {"kind": 0, "mu": 0.0, "visc": False, "freestream": (1.0, np.zeros(3), 1.0), "dt": 1e-3}
+    if name == "vortex2d_p2":
+        c["nodes"], c["conn"] = W.box_mesh(2, 16, -5.0, 5.0, q=1)
+        c["p"] = 2
+        c["freestream"] = (1.0, np.array([0.5 * math.sqrt(GAMMA), 0.0, 0.0]), 1.0)
+        c["state"] = lambda x: _conserved_at(x, W.isentropic_vortex, t=0.0)
+    elif name == "ns2d_curved_p3_g2":
+        c["nodes"], c["conn"] = W.box_mesh(2, [5, 3], 0.0, 1.0, q=2, curve=0.1, seed=2)
+        c.update(p=3, kind=1, mu=0.01, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=4)
+    elif name == "tgv3d_p3":
+        c["nodes"], c["conn"] = W.box_mesh(3, [5, 5, 3], 0.0, 2 * math.pi, q=1)
+        c.update(p=3, mu=1.0 / 1600.0, visc=True, dt=2.5e-4)
+        c["state"] = lambda x: _conserved_at(x, W.taylor_green, mach=0.1)
+    elif name == "ns3d_curved_p3":
+        c["nodes"], c["conn"] = W.box_mesh(3, 3, 0.0, 1.0, q=2, curve=0.1, seed=3)
+        c.update(p=3, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=5)
+    elif name == "ns3d_walls_p2":
+        c["nodes"], c["conn"] = W.box_mesh(3, [3, 4, 2], 0.0, [1.5, 1.0, 0.5], q=2, walls_y=True, curve=0.05)
+        c.update(p=2, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=6, periods=[1.5, 1.0, 0.5])
+    elif name in ("ns3d_ogrid_p3", "euler3d_ogrid_p2"):
+        c["nodes"], c["conn"] = W.ogrid_mesh(12, 3, 2, 0.2, r_outer=3.0, first_cell=0.05)
+        rho, vel, p = W.freestream(0.2, 3.0)
+        c["freestream"] = (rho, vel, p)
+        if name == "ns3d_ogrid_p3":
+            c.update(p=3, mu=1.0 / 2300.0, visc=True)
+        else:
+            c.update(p=2)
+        nsp = (c["p"] + 1) ** 3
+        E = len(c["nodes"])
+        c["state"] = lambda x: W.perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.05, seed=0)
+    elif name == "ns3d_p1":
+        c["nodes"], c["conn"] = W.box_mesh(3, 3, 0.0, 1.0, q=1, curve=0.08, seed=8)
+        c.update(p=1, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=7)
+    elif name == "ns3d_p4_g2":
+        c["nodes"], c["conn"] = W.box_mesh(3, [3, 2, 2], 0.0, 1.0, q=2, curve=0.1, seed=9)
+        c.update(p=4, kind=1, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=8)
+    elif name == "single_element":
+        c["nodes"], c["conn"] = W.box_mesh(3, 1, 0.0, 1.0, q=1)
+        c.update(p=3, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=9)
+    else:
+        raise KeyError(name)
+    return c
+
+
+CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
+         "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element"]
+
+
+def oracle_for(c):
+    from oracle.fr import FRSolver
+    from oracle.mesh import Mesh
+    from oracle.physics import NavierStokes
+    m = Mesh(c["nodes"], c["conn"], c["p"], kind=c["kind"])
+    dim = m.dim
+    rho, vel, p = c["freestream"]
+    ph = NavierStokes(dim, mu=c["mu"], viscous=c["visc"], freestream=(rho, np.asarray(vel)[:dim], p))
+    return m, FRSolver(m, ph)
+
+
+def gpu_options(c, precision=0):
+    from paper_2501_05709_gb300 import fr as F
+    rho, vel, p = c["freestream"]
+    return F.options(order=c["p"], correction=c["kind"], precision=precision, viscous=c["visc"], mu=c["mu"],
+                     rho_inf=rho, p_inf=p, vel_inf=tuple(vel), dt=c["dt"])
