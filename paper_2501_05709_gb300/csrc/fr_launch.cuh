@@ -9,9 +9,10 @@ namespace {
 // Opt every kernel in to the full 227 KB of dynamic shared memory on its first
 // use (a launch with E == 0 does only this), so that later launches of any
 // tile size, including those recorded into a CUDA graph, need no attribute call.
+// `done` belongs to the caller's own kernel instantiation (kernels of
+// different orders share a signature, so the flag cannot live here).
 template <typename K>
-cudaError_t prep(K kernel, size_t smem) {
-    static bool done = false;
+cudaError_t prep(K kernel, size_t smem, bool& done) {
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     if (done) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -26,7 +27,8 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* 
              cudaStream_t s) {
     auto k = frk::k_traces<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_traces<FR_DIM, P, FR_REAL>(lc.epb);
-    cudaError_t e = prep(k, sm);
+    static bool done = false;
+    cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
     k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, E, lc.epb, op);
@@ -38,7 +40,8 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_visc_face<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb);
-    cudaError_t e = prep(k, sm);
+    static bool done = false;
+    cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
     k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g);
@@ -51,7 +54,8 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_residual<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb);
-    cudaError_t e = prep(k, sm);
+    static bool done = false;
+    cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
     k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g, st);

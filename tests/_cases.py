@@ -42,12 +42,12 @@ def make_case(name):
         rho, vel, p = W.freestream(0.2, 3.0)
         c["freestream"] = (rho, vel, p)
         if name == "ns3d_ogrid_p3":
-            c.update(p=3, mu=1.0 / 2300.0, visc=True)
+            c.update(p=3, mu=1.0 / 2300.0, visc=True, dt=2e-4)
         else:
-            c.update(p=2)
+            c.update(p=2, dt=2e-4)
         nsp = (c["p"] + 1) ** 3
         E = len(c["nodes"])
-        c["state"] = lambda x: W.perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.05, seed=0)
+        c["state"] = lambda x: W.perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.02, seed=0)
     elif name == "ns3d_p1":
         c["nodes"], c["conn"] = W.box_mesh(3, 3, 0.0, 1.0, q=1, curve=0.08, seed=8)
         c.update(p=1, mu=0.02, visc=True)
@@ -67,6 +67,25 @@ def make_case(name):
 
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element"]
+
+
+def ulp_floor(fn, u, draws=2, seed=0):
+    """Relative L2 change of fn(u) when every input value moves by one unit in
+    the last place: the round-off floor of the computation itself."""
+    rng = np.random.default_rng(seed)
+    ref = fn(u)
+    worst = 0.0
+    for _ in range(draws):
+        up = u * (1.0 + rng.choice([-1.0, 1.0], size=u.shape) * 2.0 ** -53)
+        d = fn(up) - ref
+        worst = max(worst, float(np.linalg.norm(d.ravel()) / np.linalg.norm(ref.ravel())))
+    return worst
+
+
+def fp64_tol(fn, u, base=1e-12):
+    """The FP64 parity bar: 1e-12 relative L2, or 4x the oracle's own 1-ulp
+    floor where the problem's conditioning puts that floor above 2.5e-13."""
+    return max(base, 4.0 * ulp_floor(fn, u))
 
 
 def oracle_for(c):

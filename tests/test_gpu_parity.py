@@ -3,7 +3,7 @@ by element on seeded inputs (FP64: relative L2 <= 1e-12)."""
 import numpy as np
 import pytest
 
-from ._cases import CASES, gpu_options, make_case, oracle_for
+from ._cases import CASES, fp64_tol, gpu_options, make_case, oracle_for
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_residual_fp64(name):
         F.fr_residual(ctx, ud, Rd)
         torch.cuda.synchronize()
         R = Rd.cpu().numpy()
-    assert relerr(R, R_or) <= 1e-12
+    assert relerr(R, R_or) <= fp64_tol(s.residual, u)
 
 
 @pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2"])
@@ -56,7 +56,13 @@ def test_rk4_steps_fp64(name):
         F.fr_state_set(ctx, u)
         F.fr_rk_step(ctx, 3)
         out = F.fr_state_get(ctx)
-    assert relerr(out - u, ref - u) <= 1e-11
+
+    def three_steps(v):
+        for _ in range(3):
+            v = s.rk4_step(v, c["dt"])
+        return v - u
+
+    assert relerr(out - u, ref - u) <= fp64_tol(three_steps, u, base=1e-11)
     assert relerr(out, ref) <= 1e-14
 
 
@@ -184,6 +190,7 @@ def test_autotune_keeps_results():
     m, s = oracle_for(c)
     u = c["state"](m.xsp)
     R_or = s.residual(u)
+    tol = fp64_tol(s.residual, u)
     with _load(c) as ctx:
         F.fr_state_set(ctx, u)
         F.fr_autotune(ctx)
@@ -193,4 +200,4 @@ def test_autotune_keeps_results():
             Rd = torch.empty_like(ud)
             F.fr_residual(ctx, ud, Rd)
             torch.cuda.synchronize()
-            assert relerr(Rd.cpu().numpy(), R_or) <= 1e-12
+            assert relerr(Rd.cpu().numpy(), R_or) <= tol
