@@ -198,6 +198,30 @@ int fwh_integrate(const double* hist, int nt, int npts, const double* y, const d
                   int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
                   void* stream);
 
+/* fwh_integrate_noalloc: the paper has no counterpart; this is a library
+ * convenience.  Same arguments, results and errors as fwh_integrate, but it
+ * allocates no device memory: its scratch lives in one fixed device array
+ * of 2^22 doubles (32 MiB) that the library reserves on every GPU it is
+ * loaded on, until the process exits.  It is for callers that cannot call
+ * cudaMalloc/cudaFree, e.g. an application whose device memory is all owned
+ * by its own pool allocator, or one that must not pay the device-wide
+ * synchronisation of cudaFree in the middle of its work.
+ *   - Limit: 8*npts*nt + ceil(npts / max(1, 1024/ncopies)) * (longest
+ *     observer window) must not exceed 2^22; larger problems get FR_EINVAL
+ *     with a message naming the sizes (use fwh_integrate for them).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls that overlap on
+ *     the GPU (other streams or threads) race and give wrong results.  Each
+ *     call writes all the scratch it reads, so nothing needs clearing.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
+int fwh_integrate_noalloc(const double* hist, int nt, int npts, const double* y, const double* n,
+                          const double* dS, double dtau, double tau0, const double* obs, int nobs,
+                          const double Minf[3], double c0, double rho0, double p0, double Lspan,
+                          int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
+                          void* stream);
+
 /* Elements per thread block used by the residual kernels (0 = built-in
  * default); fr_autotune times the candidates on the current state and keeps
  * the fastest per kernel, returning it in *best. */

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -261,6 +262,130 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     cudaFree(X);
     cudaFree(partial);
+    if (err != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, cudaGetErrorString(err));
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fwh_integrate_noalloc: the same computation with its scratch (the source
+// series and the partial sums) in a fixed file-scope device array, for callers
+// that cannot call cudaMalloc/cudaFree.  Host code must not pass the array's
+// name to a kernel (on the host it is only a stand-in); its device address is
+// looked up once per device with cudaGetSymbolAddress and cached.
+
+namespace {
+
+constexpr size_t kNoallocScratchDoubles = size_t(1) << 22;  // 32 MiB per device
+__device__ __align__(256) double g_fwh_scratch[kNoallocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_fwh_scratch on the current device (set-up on first use).
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, "no current CUDA device");
+    if (dev < 0 || dev >= kMaxDevices) return fr_set_error_from_fwh(FR_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fwh_scratch);
+        if (e != cudaSuccess || !p)
+            return fr_set_error_from_fwh(FR_ECUDA, (std::string("cudaGetSymbolAddress of the FW-H scratch: ") +
+                                                    cudaGetErrorString(e)).c_str());
+        g_scratch_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" int fwh_integrate_noalloc(const double* hist, int nt, int npts, const double* y, const double* n,
+                                     const double* dS, double dtau, double tau0, const double* obs, int nobs,
+                                     const double Minf[3], double c0, double rho0, double p0, double Lspan,
+                                     int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
+                                     void* stream) {
+    if (!hist || !y || !n || !dS || !obs || !Minf || !p_out || !nt_out || !t0_out)
+        return fr_set_error_from_fwh(FR_EINVAL, "null argument");
+    if (nt < 5 || npts < 1 || nobs < 1 || cap < 1 || ncopies < 1 || ncopies % 2 == 0 || !(dtau > 0.0) ||
+        !(c0 > 0.0))
+        return fr_set_error_from_fwh(FR_EINVAL, "bad sizes (nt >= 5, odd ncopies, dtau > 0, c0 > 0 required)");
+    const double MM = Minf[0] * Minf[0] + Minf[1] * Minf[1] + Minf[2] * Minf[2];
+    if (!(MM < 1.0)) return fr_set_error_from_fwh(FR_EINVAL, "|Minf| must be below 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FwhConst k;
+    for (int i = 0; i < 3; ++i) k.M[i] = Minf[i];
+    k.c0 = c0;
+    k.rho0 = rho0;
+    k.p0 = p0;
+    k.dtau = dtau;
+    k.tau0 = tau0;
+    k.b2 = 1.0 / (1.0 - MM);
+    std::vector<double> yh(size_t(npts) * 3);
+    if (cudaMemcpyAsync(yh.data(), y, yh.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fr_set_error_from_fwh(FR_ECUDA, "cannot read panel positions");
+    const int K = (ncopies - 1) / 2;
+    std::vector<double> tstart(nobs);
+    std::vector<int> Tn(nobs);
+    for (int o = 0; o < nobs; ++o) {
+        double dmax = -1e300, dmin = 1e300;
+        for (int p = 0; p < npts; ++p)
+            for (int cc = -K; cc <= K; ++cc) {
+                double r[3] = {obs[o * 3 + 0] - yh[p * 3 + 0], obs[o * 3 + 1] - yh[p * 3 + 1],
+                               obs[o * 3 + 2] - (yh[p * 3 + 2] + cc * Lspan)};
+                double Mr = 0, rr = 0;
+                for (int i = 0; i < 3; ++i) {
+                    Mr += Minf[i] * r[i];
+                    rr += r[i] * r[i];
+                }
+                const double Rs = std::sqrt(rr + k.b2 * Mr * Mr) / std::sqrt(k.b2);
+                const double d = k.b2 * (Rs - Mr) / c0;
+                dmax = std::max(dmax, d);
+                dmin = std::min(dmin, d);
+            }
+        const double ts = tau0 + dmax;
+        const double te = tau0 + (nt - 1) * dtau + dmin;
+        if (te < ts) return fr_set_error_from_fwh(FR_EWINDOW, "empty observer window");
+        const int T = int(std::floor((te - ts) / dtau + 1e-9)) + 1;
+        if (T > cap) return fr_set_error_from_fwh(FR_EWINDOW, "observer window longer than the output capacity");
+        tstart[o] = ts;
+        Tn[o] = T;
+    }
+    const int group = std::max(1, 1024 / ncopies);
+    const int ngroups = (npts + group - 1) / group;
+    if (ngroups > 65535) return fr_set_error_from_fwh(FR_EINVAL, "too many panels for one launch");
+    const int Tmax = *std::max_element(Tn.begin(), Tn.end());
+    // the series (8 per panel and source time) and one partial row per panel
+    // group must fit the fixed scratch; both are fully written before any read
+    const size_t need = size_t(npts) * NSER * nt + size_t(ngroups) * Tmax;
+    if (need > kNoallocScratchDoubles)
+        return fr_set_error_from_fwh(
+            FR_EINVAL, ("fwh_integrate_noalloc: needs " + std::to_string(need) + " doubles of scratch, the fixed "
+                        "maximum is " + std::to_string(kNoallocScratchDoubles) +
+                        " (8*npts*nt + ceil(npts/max(1,1024/ncopies))*window); use fwh_integrate").c_str());
+    double* X = nullptr;
+    const int rc = noalloc_scratch(&X);
+    if (rc != FR_OK) return rc;
+    double* partial = X + size_t(npts) * NSER * nt;
+    const int64_t nw = int64_t(nt) * npts;
+    k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
+    const size_t sm = sizeof(double) * size_t(group) * ncopies * (NSER + 1);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && sm > 48 * 1024)
+        err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
+        dim3 grid(unsigned((Tn[o] + 255) / 256), unsigned(ngroups));
+        k_fwh_accum<<<grid, 256, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
+                                          tstart[o], Tn[o], ncopies, Lspan, group, partial);
+        k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
+        err = cudaGetLastError();
+        nt_out[o] = Tn[o];
+        t0_out[o] = tstart[o];
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, cudaGetErrorString(err));
     return FR_OK;
 }

@@ -78,6 +78,10 @@ _SIGS = {
     "fwh_integrate": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                 C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                 C.c_double, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fwh_integrate_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_double, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
