@@ -49,9 +49,10 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n=4, min_seconds=10.0, max_steps=50):
+def oracle_sample(n=4, min_seconds=10.0, max_steps=10000, warmup=1):
     """FP64 numpy oracle: RK4 steps of the same TGV workload on an n^3 box,
-    one BLAS thread; returns (DOF*stages/s, steps, seconds, dof)."""
+    one BLAS thread, for at least min_seconds (and at most max_steps steps);
+    returns (DOF*stages/s, steps, seconds, dof)."""
     import numpy as np
 
     from oracle.fr import FRSolver
@@ -62,7 +63,8 @@ def oracle_sample(n=4, min_seconds=10.0, max_steps=50):
     m = Mesh(nodes, conn, 3)
     s = FRSolver(m, NavierStokes(3, mu=1.0 / 1600.0))
     u = np.ascontiguousarray(np.moveaxis(W.taylor_green(m.xsp, mach=MACH), 0, 1))
-    u = s.rk4_step(u, DT)  # warm-up
+    for _ in range(max(warmup, 0)):
+        u = s.rk4_step(u, DT)
     t0 = time.perf_counter()
     k = 0
     while k < max_steps and (time.perf_counter() - t0 < min_seconds or k == 0):
@@ -73,10 +75,11 @@ def oracle_sample(n=4, min_seconds=10.0, max_steps=50):
     return dof * 4 * k / dt, k, dt, dof
 
 
-def run_oracle_subprocess(min_seconds):
+def run_oracle_subprocess(min_seconds, max_steps=10000, warmup=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.oracle_sample(min_seconds=%f)))" % (ROOT, min_seconds))
+            "print(json.dumps(bench.oracle_sample(min_seconds=%f, max_steps=%d, warmup=%d)))"
+            % (ROOT, min_seconds, max_steps, warmup))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -162,7 +165,11 @@ def gpu_leg(args, rank, world, local_rank):
     E, nsp = ctx.nelem, ctx.nsp
     dof = E * nsp
     F.fr_state_set(ctx, u0)
-    tile = F.fr_autotune(ctx)
+    if args.tile > 0:
+        F.fr_set_tile(ctx, args.tile)
+        tile = args.tile
+    else:
+        tile = F.fr_autotune(ctx)
     F.fr_state_set(ctx, u0)
     F.fr_rk_step_graph(ctx, args.warmup, sh)
     torch.cuda.synchronize()
@@ -236,7 +243,10 @@ def gpu_leg(args, rank, world, local_rank):
     if not args.no_fp64:
         c64 = F.fr_mesh_load((nodes, conn), opts(F.FR_FP64))
         F.fr_state_set(c64, u0)
-        F.fr_autotune(c64)
+        if args.tile > 0:
+            F.fr_set_tile(c64, args.tile)
+        else:
+            F.fr_autotune(c64)
         F.fr_state_set(c64, u0)
         F.fr_rk_step_graph(c64, args.warmup, sh)
         torch.cuda.synchronize()
@@ -268,11 +278,12 @@ def gpu_leg(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -285,7 +296,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = run_oracle_subprocess(min_seconds=max(3.0, 1.0 * args.steps))
+        # each step: one RK4 step of the 4^3-element sample of the same workload
+        cb = run_oracle_subprocess(min_seconds=0.0, max_steps=args.steps, warmup=args.warmup)
         line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
