@@ -58,8 +58,12 @@ struct fr_ctx {
     frg::Ref1D ref{};
     size_t rsz = 8;                          // sizeof(Real)
     // device buffers
-    void *u0 = nullptr, *us = nullptr, *acc = nullptr, *uf = nullptr, *fvn = nullptr;
-    void *S = nullptr, *J = nullptr, *N = nullptr, *ops = nullptr;
+    void *u0 = nullptr, *us = nullptr, *acc = nullptr, *fvn = nullptr;
+    void* ufb[2] = {nullptr, nullptr};   // ping-pong flux-point traces
+    bool traces_valid = false;           // ufb[0] holds the traces of u0
+    void *S = nullptr, *J = nullptr, *N = nullptr;
+    frk::Ops<double> opd{};
+    frk::Ops<float> opf{};
     int32_t* nbr = nullptr;
     int64_t sS_e = 0, sS_k = 0, sS_sp = 0, sJ_e = 0, sJ_sp = 0, sN_f = 0, sN_fp = 0;
     int32_t* wall_ef = nullptr;
@@ -95,6 +99,13 @@ frk::Geo<Real> geo_of(const fr_ctx* c) {
     g.sN_fp = c->sN_fp;
     return g;
 }
+
+template <typename Real>
+const frk::Ops<Real>& ops_ref(const fr_ctx* c);
+template <>
+const frk::Ops<double>& ops_ref<double>(const fr_ctx* c) { return c->opd; }
+template <>
+const frk::Ops<float>& ops_ref<float>(const fr_ctx* c) { return c->opf; }
 
 template <typename Real>
 frk::Phys<Real> phys_of(const fr_ctx* c) {
@@ -134,18 +145,16 @@ frk::Ops<Real> ops_of(const frg::Ref1D& r) {
 
 // ---- dimension dispatch of the per-TU launchers
 template <typename Real>
-int L_traces(fr_ctx* c, const Real* u, cudaStream_t s) {
-    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
-    Real* uf = static_cast<Real*>(c->uf);
+int L_traces(fr_ctx* c, const Real* u, Real* uf, cudaStream_t s) {
+    const auto& op = ops_ref<Real>(c);
     ++c->launches;
     return c->dim == 2 ? frl::traces<Real, 2>(c->p, u, uf, c->E, op, c->lc[0], s)
                        : frl::traces<Real, 3>(c->p, u, uf, c->E, op, c->lc[0], s);
 }
 
 template <typename Real>
-int L_visc(fr_ctx* c, const Real* u, cudaStream_t s) {
-    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
-    const Real* uf = static_cast<const Real*>(c->uf);
+int L_visc(fr_ctx* c, const Real* u, const Real* uf, cudaStream_t s) {
+    const auto& op = ops_ref<Real>(c);
     Real* fvn = static_cast<Real*>(c->fvn);
     const auto ph = phys_of<Real>(c);
     const auto g = geo_of<Real>(c);
@@ -155,9 +164,8 @@ int L_visc(fr_ctx* c, const Real* u, cudaStream_t s) {
 }
 
 template <typename Real>
-int L_resid(fr_ctx* c, const Real* u, const frk::Stage<Real>& st, cudaStream_t s) {
-    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
-    const Real* uf = static_cast<const Real*>(c->uf);
+int L_resid(fr_ctx* c, const Real* u, const Real* uf, const frk::Stage<Real>& st, cudaStream_t s) {
+    const auto& op = ops_ref<Real>(c);
     const Real* fvn = static_cast<const Real*>(c->fvn);
     const auto ph = phys_of<Real>(c);
     const auto g = geo_of<Real>(c);
@@ -169,15 +177,15 @@ int L_resid(fr_ctx* c, const Real* u, const frk::Stage<Real>& st, cudaStream_t s
 template <typename Real>
 int L_forces(fr_ctx* c, cudaStream_t s) {
     if (c->wall_off.empty() || c->wall_off.back() == 0) return 0;
-    auto op = static_cast<const frk::Ops<Real>*>(c->ops);
+    const auto& op = ops_ref<Real>(c);
     const auto g = geo_of<Real>(c);
     const Real gm1 = Real(c->opt.gamma - 1.0);
     ++c->launches;
     return c->dim == 2
-               ? frl::forces<Real, 2>(c->p, static_cast<const Real*>(c->uf), static_cast<const Real*>(c->fvn),
+               ? frl::forces<Real, 2>(c->p, static_cast<const Real*>(c->ufb[0]), static_cast<const Real*>(c->fvn),
                                       c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
                                       c->fsum, c->fcnt, s)
-               : frl::forces<Real, 3>(c->p, static_cast<const Real*>(c->uf), static_cast<const Real*>(c->fvn),
+               : frl::forces<Real, 3>(c->p, static_cast<const Real*>(c->ufb[0]), static_cast<const Real*>(c->fvn),
                                       c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
                                       c->fsum, c->fcnt, s);
 }
@@ -214,6 +222,21 @@ struct Prof {
     }
 };
 
+// Traces of u0 into ufb[0] (needed once after the state changed from outside).
+template <typename Real>
+int ensure_traces(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
+    if (c->traces_valid) return FR_OK;
+    if (pr) pr->mark_begin(0);
+    const int rc = L_traces<Real>(c, static_cast<const Real*>(c->u0), static_cast<Real*>(c->ufb[0]), s);
+    if (pr) pr->mark_end();
+    CKL(rc, "traces kernel");
+    c->traces_valid = true;
+    return FR_OK;
+}
+
+// One RK4 step; stage s reads the traces ufb[(s-1)&1] of its input and its
+// residual kernel writes the traces of its output into ufb[s&1], so the step
+// ends with the traces of the new u0 in ufb[0].
 template <typename Real>
 int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
     Real* u0 = static_cast<Real*>(c->u0);
@@ -221,13 +244,12 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
     Real* acc = static_cast<Real*>(c->acc);
     for (int stage = 1; stage <= 4; ++stage) {
         const Real* in = (stage == 1) ? u0 : us;
-        if (pr) pr->mark_begin(0);
-        int rc = L_traces<Real>(c, in, s);
-        if (pr) pr->mark_end();
-        CKL(rc, "traces kernel");
+        const Real* uf_in = static_cast<const Real*>(c->ufb[(stage - 1) & 1]);
+        Real* uf_out = static_cast<Real*>(c->ufb[stage & 1]);
+        int rc;
         if (c->visc) {
             if (pr) pr->mark_begin(1);
-            rc = L_visc<Real>(c, in, s);
+            rc = L_visc<Real>(c, in, uf_in, s);
             if (pr) pr->mark_end();
             CKL(rc, "viscous face kernel");
         }
@@ -248,28 +270,33 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         st.u0 = u0;
         st.us = us;
         st.acc = acc;
+        st.uf_next = uf_out;
         if (pr) pr->mark_begin(2);
-        rc = L_resid<Real>(c, in, st, s);
+        rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
     }
     return FR_OK;
 }
 
+// One residual of a caller state u into R; uses ufb[0], so the traces of u0
+// must be rebuilt before the next step.
 template <typename Real>
 int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
-    int rc = L_traces<Real>(c, u, s);
+    Real* uf = static_cast<Real*>(c->ufb[0]);
+    c->traces_valid = false;
+    int rc = L_traces<Real>(c, u, uf, s);
     CKL(rc, "traces kernel");
     if (c->visc) {
-        rc = L_visc<Real>(c, u, s);
+        rc = L_visc<Real>(c, u, uf, s);
         CKL(rc, "viscous face kernel");
     }
     frk::Stage<Real> st;
     st.stage = 0;
     st.dt = Real(0);
     st.R = R;
-    st.u0 = st.us = st.acc = nullptr;
-    rc = L_resid<Real>(c, u, st, s);
+    st.u0 = st.us = st.acc = st.uf_next = nullptr;
+    rc = L_resid<Real>(c, u, uf, st, s);
     CKL(rc, "residual kernel");
     return FR_OK;
 }
@@ -307,12 +334,16 @@ int orient_map(int dim, int np, int o, int fp) {
     return a + np * b;
 }
 
+size_t smem_of(const fr_ctx* c, int kernel, int epb);
+
+// default: 8 warps (elements) per block, fewer when a block would need more
+// than 96 KB of shared memory
 void default_launch(fr_ctx* c) {
-    const int target = 256;
-    int epb = std::max(1, target / c->nsp);
     for (int k = 0; k < 3; ++k) {
+        int epb = 8;
+        while (epb > 1 && smem_of(c, k, epb) > 96 * 1024) epb /= 2;
         c->lc[k].epb = epb;
-        c->lc[k].threads = target;
+        c->lc[k].threads = 32 * epb;
     }
 }
 
@@ -324,7 +355,7 @@ size_t smem_of(const fr_ctx* c, int kernel, int epb) {
 
 void release(fr_ctx* c) {
     if (!c) return;
-    void* bufs[] = {c->u0, c->us, c->acc, c->uf, c->fvn, c->S, c->J, c->N, c->ops, c->nbr,
+    void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -577,35 +608,23 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         release(c);
         return rc;
     }
-    // operators
-    if (c->prec == FR_FP64) {
-        auto op = ops_of<double>(c->ref);
-        std::vector<unsigned char> b(sizeof(op));
-        std::memcpy(b.data(), &op, sizeof(op));
-        rc = upload(&c->ops, b);
-    } else {
-        auto op = ops_of<float>(c->ref);
-        std::vector<unsigned char> b(sizeof(op));
-        std::memcpy(b.data(), &op, sizeof(op));
-        rc = upload(&c->ops, b);
-    }
-    if (rc) {
-        release(c);
-        return rc;
-    }
+    // operators (passed to kernels by value)
+    c->opd = ops_of<double>(c->ref);
+    c->opf = ops_of<float>(c->ref);
     // state and trace buffers
     const size_t nstate = size_t(E) * nv * nsp * c->rsz;
     const size_t ntrace = size_t(E) * nf * nv * nfp * c->rsz;
     if (cudaMalloc(&c->u0, nstate) != cudaSuccess || cudaMalloc(&c->us, nstate) != cudaSuccess ||
-        cudaMalloc(&c->acc, nstate) != cudaSuccess || cudaMalloc(&c->uf, ntrace) != cudaSuccess ||
-        cudaMalloc(&c->fvn, ntrace) != cudaSuccess) {
+        cudaMalloc(&c->acc, nstate) != cudaSuccess || cudaMalloc(&c->ufb[0], ntrace) != cudaSuccess ||
+        cudaMalloc(&c->ufb[1], ntrace) != cudaSuccess || cudaMalloc(&c->fvn, ntrace) != cudaSuccess) {
         release(c);
         return fail(FR_ENOMEM, "cudaMalloc failed for the state buffers");
     }
     cudaMemset(c->u0, 0, nstate);
     cudaMemset(c->us, 0, nstate);
     cudaMemset(c->acc, 0, nstate);
-    cudaMemset(c->uf, 0, ntrace);
+    cudaMemset(c->ufb[0], 0, ntrace);
+    cudaMemset(c->ufb[1], 0, ntrace);
     cudaMemset(c->fvn, 0, ntrace);
     c->partial_blocks = 1024;
     if (cudaMalloc(&c->fnow, sizeof(double) * 3 * ncand) != cudaSuccess ||
@@ -629,15 +648,15 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         c->E = 0;
         int r0, r1, r2;
         if (c->prec == FR_FP64) {
-            frk::Stage<double> st{0, 0.0, nullptr, nullptr, nullptr, nullptr};
-            r0 = L_traces<double>(c, nullptr, nullptr);
-            r1 = L_visc<double>(c, nullptr, nullptr);
-            r2 = L_resid<double>(c, nullptr, st, nullptr);
+            frk::Stage<double> st{0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr};
+            r0 = L_traces<double>(c, nullptr, nullptr, nullptr);
+            r1 = L_visc<double>(c, nullptr, nullptr, nullptr);
+            r2 = L_resid<double>(c, nullptr, nullptr, st, nullptr);
         } else {
-            frk::Stage<float> st{0, 0.0f, nullptr, nullptr, nullptr, nullptr};
-            r0 = L_traces<float>(c, nullptr, nullptr);
-            r1 = L_visc<float>(c, nullptr, nullptr);
-            r2 = L_resid<float>(c, nullptr, st, nullptr);
+            frk::Stage<float> st{0, 0.0f, nullptr, nullptr, nullptr, nullptr, nullptr};
+            r0 = L_traces<float>(c, nullptr, nullptr, nullptr);
+            r1 = L_visc<float>(c, nullptr, nullptr, nullptr);
+            r2 = L_resid<float>(c, nullptr, nullptr, st, nullptr);
         }
         c->E = keepE;
         c->launches = 0;
@@ -700,6 +719,7 @@ extern "C" int fr_state_set(fr_ctx* c, int cand, const double* u, int on_device,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = count * c->nv * c->nsp;
     char* dst = static_cast<char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
+    c->traces_valid = false;
     if (c->prec == FR_FP64) {
         CK(cudaMemcpyAsync(dst, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     } else if (on_device) {
@@ -767,8 +787,10 @@ extern "C" int fr_residual(fr_ctx* c, const void* u, void* R, void* stream) {
 extern "C" int fr_rk_step(fr_ctx* c, int nsteps, void* stream) {
     if (!c || nsteps < 0) return fail(FR_EINVAL, "bad argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = c->prec == FR_FP64 ? ensure_traces<double>(c, s) : ensure_traces<float>(c, s);
+    if (rc) return rc;
     for (int k = 0; k < nsteps; ++k) {
-        const int rc = c->prec == FR_FP64 ? enqueue_step<double>(c, s) : enqueue_step<float>(c, s);
+        rc = c->prec == FR_FP64 ? enqueue_step<double>(c, s) : enqueue_step<float>(c, s);
         if (rc) return rc;
     }
     return FR_OK;
@@ -777,6 +799,10 @@ extern "C" int fr_rk_step(fr_ctx* c, int nsteps, void* stream) {
 extern "C" int fr_rk_step_graph(fr_ctx* c, int nsteps, void* stream) {
     if (!c || nsteps < 0) return fail(FR_EINVAL, "bad argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        const int rc = c->prec == FR_FP64 ? ensure_traces<double>(c, s) : ensure_traces<float>(c, s);
+        if (rc) return rc;
+    }
     if (!c->gexec) {
         // make sure every kernel attribute is set before capture
         CK(cudaStreamSynchronize(s));
@@ -851,14 +877,14 @@ extern "C" int fr_integrals(fr_ctx* c, int cand, double* out) {
     const int nb = int(std::min<int64_t>(c->partial_blocks, std::max<int64_t>(1, (count * c->nsp + 255) / 256)));
     if (c->prec == FR_FP64) {
         auto g = geo_of<double>(c);
-        auto op = static_cast<const frk::Ops<double>*>(c->ops);
+        const auto& op = c->opd;
         rc = c->dim == 2 ? frl::integrals<double, 2>(c->p, static_cast<const double*>(c->u0), first, count, op, g,
                                                      c->partial, nb, nullptr)
                          : frl::integrals<double, 3>(c->p, static_cast<const double*>(c->u0), first, count, op, g,
                                                      c->partial, nb, nullptr);
     } else {
         auto g = geo_of<float>(c);
-        auto op = static_cast<const frk::Ops<float>*>(c->ops);
+        const auto& op = c->opf;
         rc = c->dim == 2 ? frl::integrals<float, 2>(c->p, static_cast<const float*>(c->u0), first, count, op, g,
                                                     c->partial, nb, nullptr)
                          : frl::integrals<float, 3>(c->p, static_cast<const float*>(c->u0), first, count, op, g,
@@ -1053,14 +1079,15 @@ extern "C" int fwh_clear(fr_ctx* c, int handle) {
 
 // ---------------------------------------------------------------- tiles
 extern "C" int fr_set_tile(fr_ctx* c, int epb) {
-    if (!c || epb < 0 || epb > 64) return fail(FR_EINVAL, "bad tile");
+    if (!c || epb < 0 || epb > 32) return fail(FR_EINVAL, "bad tile (elements per block 0..32)");
     if (epb == 0) {
         default_launch(c);
     } else {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 3; ++k)
             if (smem_of(c, k, epb) > 227 * 1024) return fail(FR_EINVAL, "tile needs too much shared memory");
+        for (int k = 0; k < 3; ++k) {
             c->lc[k].epb = epb;
-            c->lc[k].threads = std::min(512, std::max(64, ((epb * c->nsp + 31) / 32) * 32));
+            c->lc[k].threads = 32 * epb;
         }
     }
     invalidate_graph(c);
@@ -1069,9 +1096,9 @@ extern "C" int fr_set_tile(fr_ctx* c, int epb) {
 
 extern "C" int fr_autotune(fr_ctx* c, int* best) {
     if (!c) return fail(FR_EINVAL, "null argument");
-    // time each kernel for candidate tiles on the current state; keep the fastest
+    // time each sweep for 1..16 elements (warps) per block on the current
+    // state; keep the fastest per kernel.  Results do not depend on the tile.
     const int cand[] = {1, 2, 4, 8, 16};
-    const int threads_opts[] = {128, 256, 512};
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
@@ -1080,57 +1107,54 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
     void* R = nullptr;
     const size_t nstate = size_t(c->E) * c->nv * c->nsp * c->rsz;
     if (cudaMalloc(&R, nstate) != cudaSuccess) return fail(FR_ENOMEM, "autotune scratch");
-    const frk::Launch saved[3] = {c->lc[0], c->lc[1], c->lc[2]};
+    c->traces_valid = false;
     for (int epb : cand) {
-        for (int th : threads_opts) {
-            if (th > 1024) continue;
-            bool fits = true;
-            for (int k = 0; k < 3; ++k) fits = fits && smem_of(c, k, epb) <= 200 * 1024;
-            if (!fits) continue;
-            for (int k = 0; k < 3; ++k) c->lc[k] = frk::Launch{epb, th};
-            // warm-up then time each kernel separately (5 reps)
-            for (int kern = 0; kern < 3; ++kern) {
-                if (kern == 1 && !c->visc) continue;
-                float tot = 0;
-                for (int rep = 0; rep < 6; ++rep) {
-                    CK(cudaEventRecord(a, nullptr));
-                    int rc = 0;
-                    if (c->prec == FR_FP64) {
-                        const double* u = static_cast<const double*>(c->u0);
-                        if (kern == 0) rc = L_traces<double>(c, u, nullptr);
-                        else if (kern == 1) rc = L_visc<double>(c, u, nullptr);
-                        else {
-                            frk::Stage<double> st{0, 0.0, static_cast<double*>(R), nullptr, nullptr, nullptr};
-                            rc = L_resid<double>(c, u, st, nullptr);
-                        }
-                    } else {
-                        const float* u = static_cast<const float*>(c->u0);
-                        if (kern == 0) rc = L_traces<float>(c, u, nullptr);
-                        else if (kern == 1) rc = L_visc<float>(c, u, nullptr);
-                        else {
-                            frk::Stage<float> st{0, 0.0f, static_cast<float*>(R), nullptr, nullptr, nullptr};
-                            rc = L_resid<float>(c, u, st, nullptr);
-                        }
+        bool fits = true;
+        for (int k = 0; k < 3; ++k) fits = fits && smem_of(c, k, epb) <= 200 * 1024;
+        if (!fits) continue;
+        for (int k = 0; k < 3; ++k) c->lc[k] = frk::Launch{epb, 32 * epb};
+        for (int kern = 0; kern < 3; ++kern) {
+            if (kern == 1 && !c->visc) continue;
+            float tot = 0;
+            int rc = 0;
+            for (int rep = 0; rep < 6 && rc == 0; ++rep) {
+                CK(cudaEventRecord(a, nullptr));
+                if (c->prec == FR_FP64) {
+                    const double* u = static_cast<const double*>(c->u0);
+                    double* uf = static_cast<double*>(c->ufb[0]);
+                    if (kern == 0) rc = L_traces<double>(c, u, uf, nullptr);
+                    else if (kern == 1) rc = L_visc<double>(c, u, uf, nullptr);
+                    else {
+                        frk::Stage<double> st{0, 0.0, static_cast<double*>(R), nullptr, nullptr, nullptr, nullptr};
+                        rc = L_resid<double>(c, u, uf, st, nullptr);
                     }
-                    CK(cudaEventRecord(b, nullptr));
-                    CK(cudaEventSynchronize(b));
-                    if (rc) break;
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, a, b);
-                    if (rep > 0) tot += ms;
+                } else {
+                    const float* u = static_cast<const float*>(c->u0);
+                    float* uf = static_cast<float*>(c->ufb[0]);
+                    if (kern == 0) rc = L_traces<float>(c, u, uf, nullptr);
+                    else if (kern == 1) rc = L_visc<float>(c, u, uf, nullptr);
+                    else {
+                        frk::Stage<float> st{0, 0.0f, static_cast<float*>(R), nullptr, nullptr, nullptr, nullptr};
+                        rc = L_resid<float>(c, u, uf, st, nullptr);
+                    }
                 }
-                if (tot > 0 && tot < bestt[kern]) {
-                    bestt[kern] = tot;
-                    bestl[kern] = frk::Launch{epb, th};
-                }
+                CK(cudaEventRecord(b, nullptr));
+                CK(cudaEventSynchronize(b));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) tot += ms;
+            }
+            if (rc == 0 && tot > 0 && tot < bestt[kern]) {
+                bestt[kern] = tot;
+                bestl[kern] = frk::Launch{epb, 32 * epb};
             }
         }
     }
-    (void)saved;
     for (int k = 0; k < 3; ++k) c->lc[k] = bestl[k];
     cudaFree(R);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    c->traces_valid = false;
     invalidate_graph(c);
     if (best) *best = c->lc[2].epb;
     return FR_OK;
@@ -1146,7 +1170,7 @@ extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_ou
         ms_out[k] = 0.0;
         n_out[k] = 0;
     }
-    int rc = FR_OK;
+    int rc = c->prec == FR_FP64 ? ensure_traces<double>(c, pr.s, &pr) : ensure_traces<float>(c, pr.s, &pr);
     for (int k = 0; k < nsteps && rc == FR_OK; ++k)
         rc = c->prec == FR_FP64 ? enqueue_step<double>(c, pr.s, &pr) : enqueue_step<float>(c, pr.s, &pr);
     cudaError_t e = cudaStreamSynchronize(pr.s);

@@ -58,6 +58,7 @@ struct Geo {
 //   stage 2: input us;  acc += dt/3 k2;       us = u0 + dt/2 k2
 //   stage 3: input us;  acc += dt/3 k3;       us = u0 + dt k3
 //   stage 4: input us;  u0 = u0 + acc + dt/6 k4
+// uf_next (stages 1-4): traces of the stage's output state, for the next stage.
 template <typename Real>
 struct Stage {
     int stage;
@@ -66,11 +67,13 @@ struct Stage {
     Real* u0;
     Real* us;
     Real* acc;
+    Real* uf_next;
 };
 
+// One warp per element; epb elements (warps) per block.
 struct Launch {
-    int epb;          // elements per block
-    int threads;      // threads per block
+    int epb;          // elements (warps) per block
+    int threads;      // 32 * epb
 };
 
 }  // namespace frk
@@ -78,25 +81,26 @@ struct Launch {
 // Host-side launchers implemented per precision and dimension.
 namespace frl {
 
-// Each returns a cudaError_t value (0 on success).  `op` is a device pointer
-// to the Ops of the context's order and correction.
+// Each returns a cudaError_t value (0 on success).  `op` holds the 1D
+// operators of the context's order and correction (passed to the kernels as
+// __grid_constant__ parameters).
 template <typename Real, int DIM>
-int traces(int P, const Real* u, Real* uf, int64_t E, const frk::Ops<Real>* op,
+int traces(int P, const Real* u, Real* uf, int64_t E, const frk::Ops<Real>& op,
            frk::Launch lc, void* stream);
 
 template <typename Real, int DIM>
 int visc_face(int P, const Real* u, const Real* uf, Real* fvn, int64_t E,
-              const frk::Ops<Real>* op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
+              const frk::Ops<Real>& op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
               frk::Launch lc, void* stream);
 
 template <typename Real, int DIM>
 int residual(int P, const Real* u, const Real* uf, const Real* fvn, int64_t E,
-             const frk::Ops<Real>* op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
+             const frk::Ops<Real>& op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
              const frk::Stage<Real>& st, frk::Launch lc, void* stream);
 
 template <typename Real, int DIM>
 int forces(int P, const Real* uf, const Real* fvn, const int32_t* wall_ef, const int64_t* wall_off,
-           int ncand, const frk::Ops<Real>* op, const frk::Geo<Real>& g, Real gm1, int viscous,
+           int ncand, const frk::Ops<Real>& op, const frk::Geo<Real>& g, Real gm1, int viscous,
            double* fnow, double* fsum, double* fcnt, void* stream);
 
 template <typename Real, int DIM>
@@ -104,7 +108,7 @@ int sample(int P, const Real* u, const int64_t* pe, const Real* pw, int npts, co
            Real* hist, int* count, int cap, int* overflow, void* stream);
 
 template <typename Real, int DIM>
-int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>* op,
+int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,
               const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
 
 // dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual)

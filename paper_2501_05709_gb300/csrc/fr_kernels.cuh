@@ -253,68 +253,22 @@ __device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N,
     for (int v = 0; v < NV; ++v) ug[v] = ub[v];
 }
 
-template <typename Real>
-__device__ __forceinline__ void copy_ops(Ops<Real>* dst, const Ops<Real>* src) {
-    const Real* s = reinterpret_cast<const Real*>(src);
-    Real* d = reinterpret_cast<Real*>(dst);
-    constexpr int n = sizeof(Ops<Real>) / sizeof(Real);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = s[k];
-}
-
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// shared-memory footprint (bytes) of each kernel for epb elements
-template <int DIM, int P, typename Real>
-__host__ __device__ constexpr size_t smem_traces(int epb) {
+// Per-element (per-warp) shared-memory footprint of each kernel, in Reals.
+template <int DIM, int P>
+struct Smem {
     using Z = Sz<DIM, P>;
-    return align_up(sizeof(Ops<Real>), 16) + sizeof(Real) * size_t(epb) * Z::NV * Z::NSP;
-}
+    static constexpr int traces = Z::NV * Z::NSP;
+    static constexpr int visc = Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP;
+    static constexpr int resid = 2 * Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP;
+};
 template <int DIM, int P, typename Real>
-__host__ __device__ constexpr size_t smem_visc(int epb) {
-    using Z = Sz<DIM, P>;
-    return align_up(sizeof(Ops<Real>), 16) +
-           sizeof(Real) * size_t(epb) * (Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + Z::NV * DIM * Z::NSP);
-}
+__host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
 template <int DIM, int P, typename Real>
-__host__ __device__ constexpr size_t smem_resid(int epb) {
-    using Z = Sz<DIM, P>;
-    return align_up(sizeof(Ops<Real>), 16) +
-           sizeof(Real) * size_t(epb) * (Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP);
-}
-
-// ---------------------------------------------------------------- kernels
-// Sweep A: traces of the solution at all flux points.
+__host__ __device__ constexpr size_t smem_visc(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::visc; }
 template <int DIM, int P, typename Real>
-__global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int64_t E, int epb,
-                         const Ops<Real>* __restrict__ opg) {
-    using Z = Sz<DIM, P>;
-    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
-    extern __shared__ __align__(16) unsigned char smem[];
-    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
-    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
-    const int64_t e0 = int64_t(blockIdx.x) * epb;
-    const int ne = int(min(int64_t(epb), E - e0));
-    copy_ops(op, opg);
-    const Real* ug = u + e0 * NV * NSP;
-    for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
-    __syncthreads();
-    Real* ufg = uf + e0 * NF * NV * NFP;
-    for (int w = threadIdx.x; w < ne * NF * NV * NFP; w += blockDim.x) {
-        const int fp = w % NFP;
-        int t = w / NFP;
-        const int v = t % NV;
-        t /= NV;
-        const int f = t % NF;
-        const int el = t / NF;
-        const int d = f >> 1;
-        const Real* l = (f & 1) ? op->lp : op->lm;
-        const Real* s = su + (el * NV + v) * NSP;
-        Real acc = Real(0);
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
-        ufg[w] = acc;
-    }
-}
+__host__ __device__ constexpr size_t smem_resid(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::resid; }
 
 template <int DIM, typename Real>
 __device__ __forceinline__ void load_normal(const Geo<Real>& g, int64_t e, int f, int fp, Real* N) {
@@ -323,252 +277,320 @@ __device__ __forceinline__ void load_normal(const Geo<Real>& g, int64_t e, int f
     for (int i = 0; i < DIM; ++i) N[i] = p[i];
 }
 
+// ------------------------------------------------------------------ warp helpers
+// All element kernels below give one warp one element.  Operator entries are
+// read from the __grid_constant__ parameter with indices that are
+// compile-time after unrolling, so they become constant-bank operands.  The
+// xi_d = +1 face uses the mirror symmetry of the GL points: l_j(+1) =
+// l_{NP-1-j}(-1) and h_+(x_i) = h_-(x_{NP-1-i}).
+
+// copy one element's N values global -> shared; 16-byte vectors only when the
+// row length, the per-warp shared stride WS and the global address allow it
+template <int N, int WS, typename Real>
+__device__ __forceinline__ void warp_load(const Real* __restrict__ g, Real* s, int lane) {
+    constexpr bool vec_ok = (N * sizeof(Real)) % 16 == 0 && (WS * sizeof(Real)) % 16 == 0;
+    if constexpr (vec_ok) {
+        if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
+            constexpr int NV4 = int(N * sizeof(Real) / 16);
+            const float4* g4 = reinterpret_cast<const float4*>(g);
+            float4* s4 = reinterpret_cast<float4*>(s);
+            for (int k = lane; k < NV4; k += 32) s4[k] = g4[k];
+            return;
+        }
+    }
+    for (int k = lane; k < N; k += 32) s[k] = g[k];
+}
+
+// trace of variable v on face (d, side) at face point fp
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ Real trace_of(const Real* sv, const Ops<Real>& op, int d, int side, int fp) {
+    constexpr int NP = P + 1;
+    Real acc = Real(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc += op.lm[j] * sv[line_sp<DIM, NP>(d, fp, side ? NP - 1 - j : j)];
+    return acc;
+}
+
+// traces of the element state su at every flux point -> ufe [NF][NV][NFP]
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restrict__ ufe, const Ops<Real>& op,
+                                                  int lane) {
+    using Z = Sz<DIM, P>;
+    constexpr int NSP = Z::NSP, NFP = Z::NFP, NV = Z::NV;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < 2 * NV * NFP; t += 32) {
+            const int fp = t % NFP;
+            const int v = (t / NFP) % NV;
+            const int side = t / (NFP * NV);
+            ufe[2 * d * NV * NFP + t] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+// Sweep A (only after the state is set from outside): traces of u.
+template <int DIM, int P, typename Real>
+__global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int64_t E,
+                         const __grid_constant__ Ops<Real> op) {
+    using Z = Sz<DIM, P>;
+    constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (e >= E) return;
+    Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::traces;
+    warp_load<NV * NSP, Smem<DIM, P>::traces>(u + e * NV * NSP, su, lane);
+    __syncwarp();
+    warp_write_traces<DIM, P>(su, uf + e * NF * NV * NFP, op, lane);
+}
+
 // Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
 // boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
 // an adiabatic wall) is written instead.
 template <int DIM, int P, typename Real>
 __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
-                            int64_t E, int epb, const Ops<Real>* __restrict__ opg, Phys<Real> ph, Geo<Real> g) {
+                            int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
+                            const __grid_constant__ Geo<Real> g) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
     extern __shared__ __align__(16) unsigned char smem[];
-    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
-    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
-    Real* sj = su + epb * NV * NSP;           // jumps u_c - u_f   [el][f][v][fp]
-    Real* sl = sj + epb * NF * NV * NFP;      // own traces u_f    [el][f][v][fp]
-    Real* sg = sl + epb * NF * NV * NFP;      // grad_D u          [el][v][i][sp]
-    const int64_t e0 = int64_t(blockIdx.x) * epb;
-    const int ne = int(min(int64_t(epb), E - e0));
-    copy_ops(op, opg);
-    {
-        const Real* ug = u + e0 * NV * NSP;
-        for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
-    }
-    __syncthreads();
-    // P1: traces, neighbour traces, jumps
-    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
-        const int fp = w % NFP;
-        const int f = (w / NFP) % NF;
-        const int el = w / (NFP * NF);
-        const int d = f >> 1;
-        const Real* l = (f & 1) ? op->lp : op->lm;
-        Real uL[NV], uc[NV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (e >= E) return;
+    Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::visc;
+    Real* sj = su + NV * NSP;            // jumps u_c - u_f   [f][v][fp]
+    Real* sl = sj + NF * NV * NFP;       // own traces u_f    [f][v][fp]
+    Real* sg = sl + NF * NV * NFP;       // gradient          [d or i][v][sp]
+    warp_load<NV * NSP, Smem<DIM, P>::visc>(u + e * NV * NSP, su, lane);
+    __syncwarp();
+    // B: own and neighbour traces, jumps
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const Real* s = su + (el * NV + v) * NSP;
-            Real acc = Real(0);
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < 2 * NFP; t += 32) {
+            const int side = t >= NFP ? 1 : 0;
+            const int fp = t - side * NFP;
+            const int f = 2 * d + side;
+            Real uL[NV], uc[NV];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
-            uL[v] = acc;
-        }
-        const int code = g.nbr[(e0 + el) * NF + f];
-        if (code >= 0) {
-            const Real* un = uf + int64_t(code >> 3) * NV * NFP;
-            const int fpn = omap<DIM, NP>(code & 7, fp);
+            for (int v = 0; v < NV; ++v) uL[v] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+            const int code = g.nbr[e * NF + f];
+            if (code >= 0) {
+                const Real* un = uf + int64_t(code >> 3) * NV * NFP;
+                const int fpn = omap<DIM, NP>(code & 7, fp);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uc[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]);
-        } else {
-            Real N[DIM], ug[NV];
-            load_normal<DIM>(g, e0 + el, f, fp, N);
-            bc_state<DIM>(-code, uL, N, ph, ug, uc);
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            sj[((el * NF + f) * NV + v) * NFP + fp] = uc[v] - uL[v];
-            sl[((el * NF + f) * NV + v) * NFP + fp] = uL[v];
-        }
-    }
-    // P2: uncorrected physical gradient at solution points
-    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
-        const int sp = w % NSP;
-        const int el = w / NSP;
-        const int64_t e = e0 + el;
-        Real q[DIM][NV];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            int fpd, jd;
-            sp_split<DIM, NP>(sp, d, fpd, jd);
-            const Real* Drow = op->D + jd * MAXNP;
+                for (int v = 0; v < NV; ++v) uc[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]);
+            } else {
+                Real N[DIM], ug[NV];
+                load_normal<DIM>(g, e, f, fp, N);
+                bc_state<DIM>(-code, uL, N, ph, ug, uc);
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const Real* s = su + (el * NV + v) * NSP;
-                Real acc = Real(0);
-#pragma unroll
-                for (int j = 0; j < NP; ++j) acc += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
-                q[d][v] = acc;
+                sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
+                sl[(f * NV + v) * NFP + fp] = uL[v];
             }
         }
+    }
+    // C1: uncorrected reference gradient along lines: q_d = D_d u
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < NV * NFP; t += 32) {
+            const int v = t / NFP, ln = t % NFP;
+            Real s[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s[j] = su[v * NSP + line_sp<DIM, NP>(d, ln, j)];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                Real q = Real(0);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) q += op.D[i * MAXNP + j] * s[j];
+                sg[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, i)] = q;
+            }
+        }
+    }
+    __syncwarp();
+    // C2: physical gradient (1/|J|) S^T q at each solution point, in place
+    for (int sp = lane; sp < NSP; sp += 32) {
+        Real q[DIM][NV];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) q[d][v] = sg[(d * NV + v) * NSP + sp];
         Real S[DIM * DIM];
 #pragma unroll
         for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
         const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
+        for (int i = 0; i < DIM; ++i)
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) {
+            for (int v = 0; v < NV; ++v) {
                 Real acc = Real(0);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
-                sg[((el * NV + v) * DIM + i) * NSP + sp] = acc * iJ;
+                sg[(i * NV + v) * NSP + sp] = acc * iJ;
             }
     }
-    __syncthreads();
-    // P3: lifted face gradient and viscous normal flux
-    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
-        const int fp = w % NFP;
-        const int f = (w / NFP) % NF;
-        const int el = w / (NFP * NF);
-        const int64_t e = e0 + el;
-        const int d = f >> 1;
-        const bool side = (f & 1) != 0;
-        const Real* l = side ? op->lp : op->lm;
-        const Real* h = side ? op->hp : op->hm;
-        const Real nsg = side ? Real(1) : Real(-1);
-        // lifting coefficient along the line: sum_j l_j h_j S_j[d][i] / J_j
-        Real lc[DIM];
-        if (g.sS_sp == 0 && g.sJ_sp == 0) {
-            const Real lh = side ? op->lhp : op->lhm;
-            const Real iJ = Real(1) / g.J[e * g.sJ_e];
+    __syncwarp();
+    // D: lifted face gradient, viscous normal flux
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) lc[i] = nsg * lh * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
-        } else {
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < 2 * NFP; t += 32) {
+            const int side = t >= NFP ? 1 : 0;
+            const int fp = t - side * NFP;
+            const int f = 2 * d + side;
+            const Real nsg = side ? Real(1) : Real(-1);
+            // lifting coefficient along the line: nsign sum_j l_j h_j S_j[d][i] / J_j
+            Real lc[DIM];
+            if (g.sS_sp == 0 && g.sJ_sp == 0) {
+                const Real iJ = Real(1) / g.J[e * g.sJ_e];
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) lc[i] = Real(0);
+                for (int i = 0; i < DIM; ++i) lc[i] = nsg * op.lhm * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
+            } else {
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                const int sp = line_sp<DIM, NP>(d, fp, j);
-                const Real c = l[j] * h[j] / g.J[e * g.sJ_e + sp * g.sJ_sp];
+                for (int i = 0; i < DIM; ++i) lc[i] = Real(0);
 #pragma unroll
-                for (int i = 0; i < DIM; ++i) lc[i] += c * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k + sp * g.sS_sp];
+                for (int j = 0; j < NP; ++j) {
+                    const int sp = line_sp<DIM, NP>(d, fp, side ? NP - 1 - j : j);
+                    const Real c = op.lm[j] * op.hm[j] / g.J[e * g.sJ_e + sp * g.sJ_sp];
+#pragma unroll
+                    for (int i = 0; i < DIM; ++i)
+                        lc[i] += c * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k + sp * g.sS_sp];
+                }
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
             }
+            Real G[NV][DIM];
+            Real uL[NV];
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
-        }
-        Real G[NV][DIM];
-        Real uL[NV];
+            for (int v = 0; v < NV; ++v) {
+                const Real jv = sj[(f * NV + v) * NFP + fp];
+                uL[v] = sl[(f * NV + v) * NFP + fp];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const Real jv = sj[((el * NF + f) * NV + v) * NFP + fp];
-            uL[v] = sl[((el * NF + f) * NV + v) * NFP + fp];
+                for (int i = 0; i < DIM; ++i)
+                    G[v][i] = trace_of<DIM, P>(sg + (i * NV + v) * NSP, op, d, side, fp) + ph.eta * lc[i] * jv;
+            }
+            Real N[DIM];
+            load_normal<DIM>(g, e, f, fp, N);
+            const int code = g.nbr[e * NF + f];
+            Real Fv[NV][DIM];
+            if (code >= 0) {
+                visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
+            } else {
+                Real ug[NV], ub[NV];
+                bc_state<DIM>(-code, uL, N, ph, ug, ub);
+                visc_flux<DIM>(ub, G, ph.mu, ph.kappa, Fv);
+            }
+            Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) {
-                const Real* s = sg + ((el * NV + v) * DIM + i) * NSP;
+            for (int v = 0; v < NV; ++v) {
                 Real acc = Real(0);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
-                G[v][i] = acc + ph.eta * lc[i] * jv;
+                for (int i = 0; i < DIM; ++i) acc += Fv[v][i] * N[i];
+                if (v == NV - 1 && code == -FR_BC_WALL) acc = Real(0);
+                dst[v * NFP] = acc;
             }
         }
-        Real N[DIM];
-        load_normal<DIM>(g, e, f, fp, N);
-        const int code = g.nbr[e * NF + f];
-        Real Fv[NV][DIM];
-        Real out[NV];
-        if (code >= 0) {
-            visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
-        } else {
-            Real ug[NV], ub[NV];
-            bc_state<DIM>(-code, uL, N, ph, ug, ub);
-            visc_flux<DIM>(ub, G, ph.mu, ph.kappa, Fv);
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            Real acc = Real(0);
-#pragma unroll
-            for (int i = 0; i < DIM; ++i) acc += Fv[v][i] * N[i];
-            out[v] = acc;
-        }
-        if (code == -FR_BC_WALL) out[NV - 1] = Real(0);
-        Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dst[v * NFP] = out[v];
     }
 }
 
-// Sweep C: common fluxes, corrected gradient, flux divergence with FR
-// correction, residual R = -(1/|J|)[...], fused with the RK4 stage update.
+// Sweep C: common fluxes, corrected gradient, flux divergence with the FR
+// correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
+// stages) the traces of the updated state written for the next stage.
 template <int DIM, int P, typename Real>
 __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
-                           const Real* __restrict__ fvn, int64_t E, int epb,
-                           const Ops<Real>* __restrict__ opg, Phys<Real> ph, Geo<Real> g, Stage<Real> st) {
+                           const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
+                           const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
+                           const __grid_constant__ Stage<Real> st) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
     extern __shared__ __align__(16) unsigned char smem[];
-    Ops<Real>* op = reinterpret_cast<Ops<Real>*>(smem);
-    Real* su = reinterpret_cast<Real*>(smem + align_up(sizeof(Ops<Real>), 16));
-    Real* sj = su + epb * NV * NSP;           // jumps            [el][f][v][fp]
-    Real* sc = sj + epb * NF * NV * NFP;      // Fc.N - own F~.n  [el][f][v][fp]
-    Real* sF = sc + epb * NF * NV * NFP;      // F~_d             [el][d][v][sp]
-    const int64_t e0 = int64_t(blockIdx.x) * epb;
-    const int ne = int(min(int64_t(epb), E - e0));
-    copy_ops(op, opg);
-    {
-        const Real* ug = u + e0 * NV * NSP;
-        for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) su[w] = ug[w];
-    }
-    __syncthreads();
-    // P1: common normal flux (inviscid Rusanov minus common viscous) and jumps
-    for (int w = threadIdx.x; w < ne * NF * NFP; w += blockDim.x) {
-        const int fp = w % NFP;
-        const int f = (w / NFP) % NF;
-        const int el = w / (NFP * NF);
-        const int64_t e = e0 + el;
-        const int d = f >> 1;
-        const Real* l = (f & 1) ? op->lp : op->lm;
-        Real uL[NV], uR[NV], uc[NV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (e >= E) return;
+    Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::resid;
+    Real* sd = su + NV * NSP;            // divergence          [v][sp]
+    Real* sj = sd + NV * NSP;            // jumps u_c - u_f      [f][v][fp]
+    Real* sc = sj + NF * NV * NFP;       // Fc.N, then Fc.N - own [f][v][fp]
+    Real* sF = sc + NF * NV * NFP;       // q_d, then F~_d       [d][v][sp]
+    warp_load<NV * NSP, Smem<DIM, P>::resid>(u + e * NV * NSP, su, lane);
+    __syncwarp();
+    // B: common normal flux (Rusanov minus common viscous) and jumps
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const Real* s = su + (el * NV + v) * NSP;
-            Real acc = Real(0);
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < 2 * NFP; t += 32) {
+            const int side = t >= NFP ? 1 : 0;
+            const int fp = t - side * NFP;
+            const int f = 2 * d + side;
+            Real uL[NV], uR[NV], uc[NV];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
-            uL[v] = acc;
-        }
-        Real N[DIM];
-        load_normal<DIM>(g, e, f, fp, N);
-        const int code = g.nbr[e * NF + f];
-        int64_t nslot = 0;
-        int fpn = 0;
-        if (code >= 0) {
-            nslot = int64_t(code >> 3);
-            fpn = omap<DIM, NP>(code & 7, fp);
-            const Real* un = uf + nslot * NV * NFP;
+            for (int v = 0; v < NV; ++v) uL[v] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+            Real N[DIM];
+            load_normal<DIM>(g, e, f, fp, N);
+            const int code = g.nbr[e * NF + f];
+            int64_t nslot = 0;
+            int fpn = 0;
+            if (code >= 0) {
+                nslot = int64_t(code >> 3);
+                fpn = omap<DIM, NP>(code & 7, fp);
+                const Real* un = uf + nslot * NV * NFP;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    uR[v] = un[v * NFP + fpn];
+                    uc[v] = Real(0.5) * (uL[v] + uR[v]);
+                }
+            } else {
+                bc_state<DIM>(-code, uL, N, ph, uR, uc);
+            }
+            Real Fc[NV];
+            rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
+            if (ph.viscous) {
+                const Real* own = fvn + (e * NF + f) * NV * NFP + fp;
+                if (code >= 0) {
+                    const Real* nb = fvn + nslot * NV * NFP + fpn;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Fc[v] -= Real(0.5) * (own[v * NFP] - nb[v * NFP]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Fc[v] -= own[v * NFP];
+                }
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                uR[v] = un[v * NFP + fpn];
-                uc[v] = Real(0.5) * (uL[v] + uR[v]);
+                sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
+                sc[(f * NV + v) * NFP + fp] = Fc[v];
             }
-        } else {
-            bc_state<DIM>(-code, uL, N, ph, uR, uc);
-        }
-        Real Fc[NV];
-        rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
-        if (ph.viscous) {
-            const Real* own = fvn + (e * NF + f) * NV * NFP + fp;
-            if (code >= 0) {
-                const Real* nb = fvn + nslot * NV * NFP + fpn;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) Fc[v] -= Real(0.5) * (own[v * NFP] - nb[v * NFP]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) Fc[v] -= own[v * NFP];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            sj[((el * NF + f) * NV + v) * NFP + fp] = uc[v] - uL[v];
-            sc[((el * NF + f) * NV + v) * NFP + fp] = Fc[v];
         }
     }
-    __syncthreads();
-    // P2: flux at solution points, transformed: F~_d = sum_i S[d][i] (F_inv - F_vis)_i
-    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
-        const int sp = w % NSP;
-        const int el = w / NSP;
-        const int64_t e = e0 + el;
+    __syncwarp();
+    // C1 (viscous): corrected reference gradient along lines,
+    // q_d = D_d u + nsign h_f (u_c - u_f) for the two faces normal to d
+    if (ph.viscous) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            for (int t = lane; t < NV * NFP; t += 32) {
+                const int v = t / NFP, ln = t % NFP;
+                Real s[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) s[j] = su[v * NSP + line_sp<DIM, NP>(d, ln, j)];
+                const Real jL = sj[((2 * d) * NV + v) * NFP + ln];
+                const Real jR = sj[((2 * d + 1) * NV + v) * NFP + ln];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    Real q = op.hm[NP - 1 - i] * jR - op.hm[i] * jL;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) q += op.D[i * MAXNP + j] * s[j];
+                    sF[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, i)] = q;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // C2: flux at solution points, F~_d = sum_i S[d][i] (F_inv - F_vis)_i
+    for (int sp = lane; sp < NSP; sp += 32) {
         Real uu[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uu[v] = su[(el * NV + v) * NSP + sp];
+        for (int v = 0; v < NV; ++v) uu[v] = su[v * NSP + sp];
         Real S[DIM * DIM];
 #pragma unroll
         for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
@@ -586,25 +608,6 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             }
         }
         if (ph.viscous) {
-            Real q[DIM][NV];
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                int fpd, jd;
-                sp_split<DIM, NP>(sp, d, fpd, jd);
-                const Real* Drow = op->D + jd * MAXNP;
-                const Real hmv = -op->hm[jd];
-                const Real hpv = op->hp[jd];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const Real* s = su + (el * NV + v) * NSP;
-                    Real acc = Real(0);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) acc += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
-                    acc += hmv * sj[((el * NF + 2 * d) * NV + v) * NFP + fpd];
-                    acc += hpv * sj[((el * NF + 2 * d + 1) * NV + v) * NFP + fpd];
-                    q[d][v] = acc;
-                }
-            }
             const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
             Real G[NV][DIM];
 #pragma unroll
@@ -613,7 +616,7 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                 for (int i = 0; i < DIM; ++i) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
+                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * sF[(d * NV + v) * NSP + sp];
                     G[v][i] = acc * iJ;
                 }
             Real Fv[NV][DIM];
@@ -630,69 +633,81 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                 Real acc = Real(0);
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];
-                sF[((el * DIM + d) * NV + v) * NSP + sp] = acc;
+                sF[(d * NV + v) * NSP + sp] = acc;
             }
     }
-    __syncthreads();
-    // P3: flux jump at flux points: Fc.N - nsign I_f[F~_d]
-    for (int w = threadIdx.x; w < ne * NF * NV * NFP; w += blockDim.x) {
-        const int fp = w % NFP;
-        int t = w / NFP;
-        const int v = t % NV;
-        t /= NV;
-        const int f = t % NF;
-        const int el = t / NF;
-        const int d = f >> 1;
-        const bool side = (f & 1) != 0;
-        const Real* l = side ? op->lp : op->lm;
-        const Real* s = sF + ((el * DIM + d) * NV + v) * NSP;
-        Real acc = Real(0);
+    __syncwarp();
+    // D: flux jump at flux points, Fc.N - nsign I_f[F~_d]
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc += l[j] * s[line_sp<DIM, NP>(d, fp, j)];
-        Real* c = sc + ((el * NF + f) * NV + v) * NFP + fp;
-        *c = side ? (*c - acc) : (*c + acc);
-    }
-    __syncthreads();
-    // P4: divergence + correction, residual, RK stage
-    for (int w = threadIdx.x; w < ne * NV * NSP; w += blockDim.x) {
-        const int sp = w % NSP;
-        const int v = (w / NSP) % NV;
-        const int el = w / (NSP * NV);
-        const int64_t e = e0 + el;
-        Real div = Real(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            int fpd, jd;
-            sp_split<DIM, NP>(sp, d, fpd, jd);
-            const Real* Drow = op->D + jd * MAXNP;
-            const Real* s = sF + ((el * DIM + d) * NV + v) * NSP;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) div += Drow[j] * s[line_sp<DIM, NP>(d, fpd, j)];
-            div += op->hm[jd] * sc[((el * NF + 2 * d) * NV + v) * NFP + fpd];
-            div += op->hp[jd] * sc[((el * NF + 2 * d + 1) * NV + v) * NFP + fpd];
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < 2 * NV * NFP; t += 32) {
+            const int fp = t % NFP;
+            const int v = (t / NFP) % NV;
+            const int side = t / (NFP * NV);
+            const Real own = trace_of<DIM, P>(sF + (d * NV + v) * NSP, op, d, side, fp);
+            Real* c = sc + 2 * d * NV * NFP + t;
+            *c = side ? (*c - own) : (*c + own);
         }
-        const Real r = -div / g.J[e * g.sJ_e + sp * g.sJ_sp];
-        const int64_t gi = e0 * NV * NSP + w;
+    }
+    __syncwarp();
+    // E: divergence plus correction along lines, accumulated direction by direction
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        for (int t = lane; t < NV * NFP; t += 32) {
+            const int v = t / NFP, ln = t % NFP;
+            Real s[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s[j] = sF[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, j)];
+            const Real cL = sc[((2 * d) * NV + v) * NFP + ln];
+            const Real cR = sc[((2 * d + 1) * NV + v) * NFP + ln];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                Real val = op.hm[i] * cL + op.hm[NP - 1 - i] * cR;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) val += op.D[i * MAXNP + j] * s[j];
+                const int k = v * NSP + line_sp<DIM, NP>(d, ln, i);
+                sd[k] = (d == 0) ? val : sd[k] + val;
+            }
+        }
+        __syncwarp();
+    }
+    // F: residual and RK stage; the new stage state replaces su for the traces
+    const int64_t base = e * NV * NSP;
+    for (int k = lane; k < NV * NSP; k += 32) {
+        const int sp = k % NSP;
+        const Real r = -sd[k] / g.J[e * g.sJ_e + sp * g.sJ_sp];
+        const int64_t gi = base + k;
+        Real nu;
         switch (st.stage) {
             case 0:
                 st.R[gi] = r;
+                nu = su[k];
                 break;
             case 1:
                 st.acc[gi] = (st.dt * Real(1.0 / 6.0)) * r;
-                st.us[gi] = su[w] + (st.dt * Real(0.5)) * r;
+                nu = su[k] + (st.dt * Real(0.5)) * r;
+                st.us[gi] = nu;
                 break;
             case 2:
                 st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
-                st.us[gi] = st.u0[gi] + (st.dt * Real(0.5)) * r;
+                nu = st.u0[gi] + (st.dt * Real(0.5)) * r;
+                st.us[gi] = nu;
                 break;
             case 3:
                 st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
-                st.us[gi] = st.u0[gi] + st.dt * r;
+                nu = st.u0[gi] + st.dt * r;
+                st.us[gi] = nu;
                 break;
             default:
-                st.u0[gi] = st.u0[gi] + st.acc[gi] + (st.dt * Real(1.0 / 6.0)) * r;
+                nu = st.u0[gi] + st.acc[gi] + (st.dt * Real(1.0 / 6.0)) * r;
+                st.u0[gi] = nu;
                 break;
         }
+        su[k] = nu;
+    }
+    if (st.uf_next) {
+        __syncwarp();
+        warp_write_traces<DIM, P>(su, st.uf_next + e * NF * NV * NFP, op, lane);
     }
 }
 
@@ -704,7 +719,8 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
 template <int DIM, int P, typename Real>
 __global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ fvn,
                          const int32_t* __restrict__ wall_ef, const int64_t* __restrict__ wall_off,
-                         const Ops<Real>* __restrict__ op, Geo<Real> g, Real gm1, int viscous,
+                         const __grid_constant__ Ops<Real> op, const __grid_constant__ Geo<Real> g, Real gm1,
+                         int viscous,
                          double* __restrict__ fnow, double* __restrict__ fsum, double* __restrict__ fcnt) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
@@ -725,7 +741,20 @@ __global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ f
         const Real p = pressure<DIM>(uL, gm1);
         Real N[DIM];
         load_normal<DIM>(g, e, f, fp, N);
-        const double wt = (DIM == 2) ? double(op->w[fp]) : double(op->w[fp % NP]) * double(op->w[fp / NP]);
+        double wt;
+        if (DIM == 2) {
+            wt = 0.0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) if (fp == j) wt = double(op.w[j]);
+        } else {
+            double wa = 0.0, wb = 0.0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                if (fp % NP == j) wa = double(op.w[j]);
+                if (fp / NP == j) wb = double(op.w[j]);
+            }
+            wt = wa * wb;
+        }
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
             double fi = double(p) * double(N[i]);
@@ -806,7 +835,8 @@ static __global__ void k_bump(int* count, int cap, int* overflow) {
 // energy over elements [e_first, e_first + ne): one partial row per block.
 template <int DIM, int P, typename Real>
 __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t ne,
-                            const Ops<Real>* __restrict__ op, Geo<Real> g, double* __restrict__ partial) {
+                            const __grid_constant__ Ops<Real> op, const __grid_constant__ Geo<Real> g,
+                            double* __restrict__ partial) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NV = Z::NV;
     __shared__ double red[NV + 1][256];
@@ -817,8 +847,14 @@ __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t
          w += int64_t(gridDim.x) * blockDim.x) {
         const int64_t e = e_first + w / NSP;
         const int sp = int(w % NSP);
-        double wt = double(op->w[sp % NP]) * double(op->w[(sp / NP) % NP]);
-        if (DIM == 3) wt *= double(op->w[sp / (NP * NP)]);
+        double w0 = 0.0, w1 = 0.0, w2 = 1.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            if (sp % NP == j) w0 = double(op.w[j]);
+            if ((sp / NP) % NP == j) w1 = double(op.w[j]);
+            if (DIM == 3 && sp / (NP * NP) == j) w2 = double(op.w[j]);
+        }
+        double wt = w0 * w1 * w2;
         wt *= double(g.J[e * g.sJ_e + sp * g.sJ_sp]);
         const Real* ue = u + e * NV * NSP + sp;
         double m2 = 0.0;

@@ -23,7 +23,7 @@ cudaError_t prep(K kernel, size_t smem, bool& done) {
 inline unsigned grid_of(int64_t E, int epb) { return unsigned((E + epb - 1) / epb); }
 
 template <int P>
-int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* op, frk::Launch lc,
+int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& op, frk::Launch lc,
              cudaStream_t s) {
     auto k = frk::k_traces<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_traces<FR_DIM, P, FR_REAL>(lc.epb);
@@ -31,12 +31,12 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* 
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, E, lc.epb, op);
+    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, E, op);
     return int(cudaGetLastError());
 }
 
 template <int P>
-int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>* op,
+int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>& op,
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_visc_face<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb);
@@ -44,13 +44,13 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g);
+    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g);
     return int(cudaGetLastError());
 }
 
 template <int P>
 int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
-            const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
+            const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_residual<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb);
@@ -58,7 +58,7 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), lc.threads, sm, s>>>(u, uf, fvn, E, lc.epb, op, ph, g, st);
+    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g, st);
     return int(cudaGetLastError());
 }
 
@@ -74,7 +74,7 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
     }
 
 template <>
-int traces<FR_REAL, FR_DIM>(int P, const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>* op,
+int traces<FR_REAL, FR_DIM>(int P, const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& op,
                             frk::Launch lc, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 #define C(PP) traces_p<PP>(u, uf, E, op, lc, s)
@@ -84,7 +84,7 @@ int traces<FR_REAL, FR_DIM>(int P, const FR_REAL* u, FR_REAL* uf, int64_t E, con
 
 template <>
 int visc_face<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E,
-                               const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph,
+                               const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph,
                                const frk::Geo<FR_REAL>& g, frk::Launch lc, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 #define C(PP) visc_p<PP>(u, uf, fvn, E, op, ph, g, lc, s)
@@ -94,7 +94,7 @@ int visc_face<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, FR_RE
 
 template <>
 int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
-                              const frk::Ops<FR_REAL>* op, const frk::Phys<FR_REAL>& ph,
+                              const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph,
                               const frk::Geo<FR_REAL>& g, const frk::Stage<FR_REAL>& st, frk::Launch lc,
                               void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -120,7 +120,7 @@ size_t smem_bytes<FR_REAL, FR_DIM>(int P, int kernel, int epb) {
 
 template <>
 int forces<FR_REAL, FR_DIM>(int P, const FR_REAL* uf, const FR_REAL* fvn, const int32_t* wall_ef,
-                            const int64_t* wall_off, int ncand, const frk::Ops<FR_REAL>* op,
+                            const int64_t* wall_off, int ncand, const frk::Ops<FR_REAL>& op,
                             const frk::Geo<FR_REAL>& g, FR_REAL gm1, int viscous, double* fnow, double* fsum,
                             double* fcnt, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -147,7 +147,7 @@ int sample<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const int64_t* pe, const FR
 
 template <>
 int integrals<FR_REAL, FR_DIM>(int P, const FR_REAL* u, int64_t e_first, int64_t ne,
-                               const frk::Ops<FR_REAL>* op, const frk::Geo<FR_REAL>& g, double* partial,
+                               const frk::Ops<FR_REAL>& op, const frk::Geo<FR_REAL>& g, double* partial,
                                int nblocks, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 #define C(PP) (frk::k_integrals<FR_DIM, PP, FR_REAL><<<nblocks, 256, 0, s>>>(u, e_first, ne, op, g, partial), \

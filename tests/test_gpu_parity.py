@@ -201,3 +201,22 @@ def test_autotune_keeps_results():
             F.fr_residual(ctx, ud, Rd)
             torch.cuda.synchronize()
             assert relerr(Rd.cpu().numpy(), R_or) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_accepts_unaligned_buffers(precision):
+    # a caller's state may start at any element offset (e.g. a sliced tensor)
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("tgv3d_p3")
+    m, s = oracle_for(c)
+    u = c["state"](m.xsp)
+    dt = torch.float64 if precision == 0 else torch.float32
+    with _load(c, precision) as ctx:
+        big = torch.zeros(u.size + 1, dtype=dt, device="cuda")
+        big[1:] = torch.tensor(u.ravel(), dtype=dt, device="cuda")
+        Rbig = torch.zeros(u.size + 3, dtype=dt, device="cuda")
+        F.fr_residual(ctx, big[1:], Rbig[3:])
+        ref = torch.empty(u.shape, dtype=dt, device="cuda")
+        F.fr_residual(ctx, torch.tensor(u, dtype=dt, device="cuda"), ref)
+        torch.cuda.synchronize()
+    assert torch.equal(Rbig[3:].view(u.shape), ref)
