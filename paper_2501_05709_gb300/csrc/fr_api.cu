@@ -61,7 +61,7 @@ struct fr_ctx {
     void *u0 = nullptr, *us = nullptr, *acc = nullptr, *fvn = nullptr;
     void* ufb[2] = {nullptr, nullptr};   // ping-pong flux-point traces
     bool traces_valid = false;           // ufb[0] holds the traces of u0
-    void *S = nullptr, *J = nullptr, *N = nullptr;
+    void *S = nullptr, *J = nullptr, *iJ = nullptr, *N = nullptr;
     frk::Ops<double> opd{};
     frk::Ops<float> opf{};
     int32_t* nbr = nullptr;
@@ -88,6 +88,7 @@ frk::Geo<Real> geo_of(const fr_ctx* c) {
     frk::Geo<Real> g;
     g.S = static_cast<const Real*>(c->S);
     g.J = static_cast<const Real*>(c->J);
+    g.iJ = static_cast<const Real*>(c->iJ);
     g.N = static_cast<const Real*>(c->N);
     g.nbr = c->nbr;
     g.sS_e = c->sS_e;
@@ -355,7 +356,7 @@ size_t smem_of(const fr_ctx* c, int kernel, int epb) {
 
 void release(fr_ctx* c) {
     if (!c) return;
-    void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->N, c->nbr,
+    void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -577,8 +578,10 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         c->sS_e = dim * dim; c->sS_k = 1; c->sS_sp = 0;
         c->sJ_e = 1; c->sJ_sp = 0;
         c->sN_f = dim; c->sN_fp = 0;
+        std::vector<double> iJ1(J1.size());
+        for (size_t i = 0; i < J1.size(); ++i) iJ1[i] = 1.0 / J1[i];
         if ((rc = upload_real(&c->S, S1, c->prec)) || (rc = upload_real(&c->J, J1, c->prec)) ||
-            (rc = upload_real(&c->N, N1, c->prec))) {
+            (rc = upload_real(&c->iJ, iJ1, c->prec)) || (rc = upload_real(&c->N, N1, c->prec))) {
             release(c);
             return rc;
         }
@@ -586,8 +589,10 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         c->sS_e = int64_t(dim) * dim * nsp; c->sS_k = nsp; c->sS_sp = 1;
         c->sJ_e = nsp; c->sJ_sp = 1;
         c->sN_f = int64_t(nfp) * dim; c->sN_fp = dim;
+        std::vector<double> iJh(Jh.size());
+        for (size_t i = 0; i < Jh.size(); ++i) iJh[i] = 1.0 / Jh[i];
         if ((rc = upload_real(&c->S, Sh, c->prec)) || (rc = upload_real(&c->J, Jh, c->prec)) ||
-            (rc = upload_real(&c->N, Nsh, c->prec))) {
+            (rc = upload_real(&c->iJ, iJh, c->prec)) || (rc = upload_real(&c->N, Nsh, c->prec))) {
             release(c);
             return rc;
         }

@@ -38,13 +38,14 @@ struct Phys {
 // Geometry arrays with strides: an affine mesh stores one metric set per
 // element (sp/fp strides 0), a curved mesh one per solution/flux point.
 //   S[e*sS_e + k*sS_k + sp*sS_sp], k = d*DIM + i   : |J| dxi_d/dx_i
-//   J[e*sJ_e + sp*sJ_sp]                            : |J|
+//   J[e*sJ_e + sp*sJ_sp]                            : |J|   (iJ: 1/|J|, same strides)
 //   N[(e*NF + f)*sN_f + fp*sN_fp + i]               : outward area-weighted normal
 //   nbr[e*NF + f] = (ne*NF + nf)*8 + orientation, or -tag on boundary faces
 template <typename Real>
 struct Geo {
     const Real* S;
     const Real* J;
+    const Real* iJ;
     const Real* N;
     const int32_t* nbr;
     int64_t sS_e, sS_k, sS_sp;

@@ -87,7 +87,8 @@ __device__ __forceinline__ void flux_inv_n(const Real* u, Real p, const Real* n,
 }
 
 // Rusanov common flux, area-weighted: F^c.N = |N| [ (F_L + F_R).n/2 - lambda (u_R - u_L)/2 ],
-// lambda = max(|V_L.n| + c_L, |V_R.n| + c_R)
+// lambda = max(|V_L.n| + c_L, |V_R.n| + c_R); one reciprocal per state and
+// one reciprocal square root for the normal.
 template <int DIM, typename Real>
 __device__ __forceinline__ void rusanov(const Real* uL, const Real* uR, const Real* N,
                                         Real gamma, Real gm1, Real* F) {
@@ -95,22 +96,32 @@ __device__ __forceinline__ void rusanov(const Real* uL, const Real* uR, const Re
     Real a2 = Real(0);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) a2 += N[i] * N[i];
-    const Real area = sqrt(a2);
+    const Real ia = rsqrt(a2);
+    const Real area = a2 * ia;
     Real n[DIM];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) n[i] = N[i] / area;
-    const Real pL = pressure<DIM>(uL, gm1), pR = pressure<DIM>(uR, gm1);
-    Real FL[NV], FR[NV];
-    flux_inv_n<DIM>(uL, pL, n, FL);
-    flux_inv_n<DIM>(uR, pR, n, FR);
-    const Real vL = fabs(FL[0] / uL[0]);
-    const Real vR = fabs(FR[0] / uR[0]);
-    const Real cL = sqrt(gamma * pL / uL[0]);
-    const Real cR = sqrt(gamma * pR / uR[0]);
-    const Real lam = fmax(vL + cL, vR + cR);
+    for (int i = 0; i < DIM; ++i) n[i] = N[i] * ia;
+    const Real irL = Real(1) / uL[0], irR = Real(1) / uR[0];
+    Real mnL = Real(0), mnR = Real(0), m2L = Real(0), m2R = Real(0);
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-        F[v] = (Real(0.5) * (FL[v] + FR[v]) - Real(0.5) * lam * (uR[v] - uL[v])) * area;
+    for (int i = 0; i < DIM; ++i) {
+        mnL += uL[1 + i] * n[i];
+        mnR += uR[1 + i] * n[i];
+        m2L += uL[1 + i] * uL[1 + i];
+        m2R += uR[1 + i] * uR[1 + i];
+    }
+    const Real pL = gm1 * (uL[NV - 1] - Real(0.5) * m2L * irL);
+    const Real pR = gm1 * (uR[NV - 1] - Real(0.5) * m2R * irR);
+    const Real vL = mnL * irL, vR = mnR * irR;
+    const Real cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+    const Real lam = fmax(fabs(vL) + cL, fabs(vR) + cR);
+    const Real h = Real(0.5) * area;
+    const Real hl = h * lam;
+    F[0] = h * (mnL + mnR) - hl * (uR[0] - uL[0]);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+        F[1 + i] = h * (uL[1 + i] * vL + uR[1 + i] * vR + (pL + pR) * n[i]) - hl * (uR[1 + i] - uL[1 + i]);
+    F[NV - 1] = h * ((uL[NV - 1] + pL) * vL + (uR[NV - 1] + pR) * vR) - hl * (uR[NV - 1] - uL[NV - 1]);
 }
 
 // Viscous flux F_vis (Eqs. 4, 6, 7 in the standard sign: [0, tau_ij, V_i tau_ij - q_j],
@@ -301,6 +312,30 @@ __device__ __forceinline__ void warp_load(const Real* __restrict__ g, Real* s, i
     for (int k = lane; k < N; k += 32) s[k] = g[k];
 }
 
+// metric terms S[d][i] at solution point sp (affine: one set per element)
+template <int DIM, typename Real>
+__device__ __forceinline__ void load_S(const Geo<Real>& g, int64_t e, int sp, Real* S) {
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
+}
+
+// both end values of the line of sv through face point ln in direction d:
+// m = sum_j l_j(-1) s_j and p = sum_j l_j(+1) s_j
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ void line_ends(const Real* sv, const Ops<Real>& op, int d, int ln, Real& m, Real& p) {
+    constexpr int NP = P + 1;
+    Real s[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s[j] = sv[line_sp<DIM, NP>(d, ln, j)];
+    m = Real(0);
+    p = Real(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        m += op.lm[j] * s[j];
+        p += op.lm[NP - 1 - j] * s[j];
+    }
+}
+
 // trace of variable v on face (d, side) at face point fp
 template <int DIM, int P, typename Real>
 __device__ __forceinline__ Real trace_of(const Real* sv, const Ops<Real>& op, int d, int side, int fp) {
@@ -312,6 +347,7 @@ __device__ __forceinline__ Real trace_of(const Real* sv, const Ops<Real>& op, in
 }
 
 // traces of the element state su at every flux point -> ufe [NF][NV][NFP]
+// (global or shared), one line per task producing both faces of direction d
 template <int DIM, int P, typename Real>
 __device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restrict__ ufe, const Ops<Real>& op,
                                                   int lane) {
@@ -319,11 +355,12 @@ __device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restri
     constexpr int NSP = Z::NSP, NFP = Z::NFP, NV = Z::NV;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < 2 * NV * NFP; t += 32) {
-            const int fp = t % NFP;
-            const int v = (t / NFP) % NV;
-            const int side = t / (NFP * NV);
-            ufe[2 * d * NV * NFP + t] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+        for (int t = lane; t < NV * NFP; t += 32) {
+            const int v = t / NFP, ln = t % NFP;
+            Real m, p;
+            line_ends<DIM, P>(su + v * NSP, op, d, ln, m, p);
+            ufe[2 * d * NV * NFP + t] = m;
+            ufe[(2 * d + 1) * NV * NFP + t] = p;
         }
     }
 }
@@ -364,7 +401,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     Real* sg = sl + NF * NV * NFP;       // gradient          [d or i][v][sp]
     warp_load<NV * NSP, Smem<DIM, P>::visc>(u + e * NV * NSP, su, lane);
     __syncwarp();
-    // B: own and neighbour traces, jumps
+    // B: own traces (line pass), then neighbour traces and jumps per face point
+    warp_write_traces<DIM, P>(su, sl, op, lane);
+    __syncwarp();
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         for (int t = lane; t < 2 * NFP; t += 32) {
@@ -373,7 +412,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             const int f = 2 * d + side;
             Real uL[NV], uc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uL[v] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+            for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
             const int code = g.nbr[e * NF + f];
             if (code >= 0) {
                 const Real* un = uf + int64_t(code >> 3) * NV * NFP;
@@ -386,10 +425,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 bc_state<DIM>(-code, uL, N, ph, ug, uc);
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
-                sl[(f * NV + v) * NFP + fp] = uL[v];
-            }
+            for (int v = 0; v < NV; ++v) sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
         }
     }
     // C1: uncorrected reference gradient along lines: q_d = D_d u
@@ -418,9 +454,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
             for (int v = 0; v < NV; ++v) q[d][v] = sg[(d * NV + v) * NSP + sp];
         Real S[DIM * DIM];
-#pragma unroll
-        for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
-        const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
+        load_S<DIM>(g, e, sp, S);
+        const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
@@ -443,7 +478,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             // lifting coefficient along the line: nsign sum_j l_j h_j S_j[d][i] / J_j
             Real lc[DIM];
             if (g.sS_sp == 0 && g.sJ_sp == 0) {
-                const Real iJ = Real(1) / g.J[e * g.sJ_e];
+                const Real iJ = g.iJ[e * g.sJ_e];
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) lc[i] = nsg * op.lhm * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
             } else {
@@ -452,7 +487,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
                     const int sp = line_sp<DIM, NP>(d, fp, side ? NP - 1 - j : j);
-                    const Real c = op.lm[j] * op.hm[j] / g.J[e * g.sJ_e + sp * g.sJ_sp];
+                    const Real c = op.lm[j] * op.hm[j] * g.iJ[e * g.sJ_e + sp * g.sJ_sp];
 #pragma unroll
                     for (int i = 0; i < DIM; ++i)
                         lc[i] += c * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k + sp * g.sS_sp];
@@ -504,6 +539,8 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                            const __grid_constant__ Stage<Real> st) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    constexpr int NSPW = (NSP + 31) / 32;           // solution points per lane
+    constexpr bool PREFETCH = NSPW <= 2;            // RK arrays held in registers
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
@@ -512,8 +549,29 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
     Real* sd = su + NV * NSP;            // divergence          [v][sp]
     Real* sj = sd + NV * NSP;            // jumps u_c - u_f      [f][v][fp]
     Real* sc = sj + NF * NV * NFP;       // Fc.N, then Fc.N - own [f][v][fp]
-    Real* sF = sc + NF * NV * NFP;       // q_d, then F~_d       [d][v][sp]
-    warp_load<NV * NSP, Smem<DIM, P>::resid>(u + e * NV * NSP, su, lane);
+    Real* sF = sc + NF * NV * NFP;       // own traces, q_d, then F~_d  [d][v][sp]
+    const int64_t base = e * NV * NSP;
+    warp_load<NV * NSP, Smem<DIM, P>::resid>(u + base, su, lane);
+    // the RK stage arrays are only needed at the end: issue their loads now
+    Real pu0[NSPW][NV], pacc[NSPW][NV];
+    if constexpr (PREFETCH) {
+        if (st.stage >= 2) {
+#pragma unroll
+            for (int s = 0; s < NSPW; ++s) {
+                const int sp = lane + 32 * s;
+                if (sp < NSP)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        pu0[s][v] = st.u0[base + v * NSP + sp];
+                        pacc[s][v] = st.acc[base + v * NSP + sp];
+                    }
+            }
+        }
+    }
+    __syncwarp();
+    // B0: own traces of every face, one line pass (into the sF area)
+    Real* sl = sF;
+    warp_write_traces<DIM, P>(su, sl, op, lane);
     __syncwarp();
     // B: common normal flux (Rusanov minus common viscous) and jumps
 #pragma unroll
@@ -524,7 +582,7 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             const int f = 2 * d + side;
             Real uL[NV], uR[NV], uc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uL[v] = trace_of<DIM, P>(su + v * NSP, op, d, side, fp);
+            for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
             Real N[DIM];
             load_normal<DIM>(g, e, f, fp, N);
             const int code = g.nbr[e * NF + f];
@@ -592,23 +650,23 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
 #pragma unroll
         for (int v = 0; v < NV; ++v) uu[v] = su[v * NSP + sp];
         Real S[DIM * DIM];
-#pragma unroll
-        for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
+        load_S<DIM>(g, e, sp, S);
         Real F[NV][DIM];
-        const Real p = pressure<DIM>(uu, ph.gm1);
-        {
-            const Real ir = Real(1) / uu[0];
+        const Real ir = Real(1) / uu[0];
+        Real m2 = Real(0);
 #pragma unroll
-            for (int j = 0; j < DIM; ++j) {
-                const Real vj = uu[1 + j] * ir;
-                F[0][j] = uu[1 + j];
+        for (int i = 0; i < DIM; ++i) m2 += uu[1 + i] * uu[1 + i];
+        const Real p = ph.gm1 * (uu[NV - 1] - Real(0.5) * m2 * ir);
 #pragma unroll
-                for (int i = 0; i < DIM; ++i) F[1 + i][j] = uu[1 + i] * vj + (i == j ? p : Real(0));
-                F[NV - 1][j] = (uu[NV - 1] + p) * vj;
-            }
+        for (int j = 0; j < DIM; ++j) {
+            const Real vj = uu[1 + j] * ir;
+            F[0][j] = uu[1 + j];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) F[1 + i][j] = uu[1 + i] * vj + (i == j ? p : Real(0));
+            F[NV - 1][j] = (uu[NV - 1] + p) * vj;
         }
         if (ph.viscous) {
-            const Real iJ = Real(1) / g.J[e * g.sJ_e + sp * g.sJ_sp];
+            const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
             Real G[NV][DIM];
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -637,16 +695,15 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             }
     }
     __syncwarp();
-    // D: flux jump at flux points, Fc.N - nsign I_f[F~_d]
+    // D: flux jump at both faces of each line, Fc.N - nsign I_f[F~_d]
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < 2 * NV * NFP; t += 32) {
-            const int fp = t % NFP;
-            const int v = (t / NFP) % NV;
-            const int side = t / (NFP * NV);
-            const Real own = trace_of<DIM, P>(sF + (d * NV + v) * NSP, op, d, side, fp);
-            Real* c = sc + 2 * d * NV * NFP + t;
-            *c = side ? (*c - own) : (*c + own);
+        for (int t = lane; t < NV * NFP; t += 32) {
+            const int v = t / NFP, ln = t % NFP;
+            Real m, pp;
+            line_ends<DIM, P>(sF + (d * NV + v) * NSP, op, d, ln, m, pp);
+            sc[2 * d * NV * NFP + t] += m;
+            sc[(2 * d + 1) * NV * NFP + t] -= pp;
         }
     }
     __syncwarp();
@@ -671,39 +728,56 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
         }
         __syncwarp();
     }
-    // F: residual and RK stage; the new stage state replaces su for the traces
-    const int64_t base = e * NV * NSP;
-    for (int k = lane; k < NV * NSP; k += 32) {
-        const int sp = k % NSP;
-        const Real r = -sd[k] / g.J[e * g.sJ_e + sp * g.sJ_sp];
-        const int64_t gi = base + k;
-        Real nu;
-        switch (st.stage) {
-            case 0:
-                st.R[gi] = r;
-                nu = su[k];
-                break;
-            case 1:
-                st.acc[gi] = (st.dt * Real(1.0 / 6.0)) * r;
-                nu = su[k] + (st.dt * Real(0.5)) * r;
-                st.us[gi] = nu;
-                break;
-            case 2:
-                st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
-                nu = st.u0[gi] + (st.dt * Real(0.5)) * r;
-                st.us[gi] = nu;
-                break;
-            case 3:
-                st.acc[gi] += (st.dt * Real(1.0 / 3.0)) * r;
-                nu = st.u0[gi] + st.dt * r;
-                st.us[gi] = nu;
-                break;
-            default:
-                nu = st.u0[gi] + st.acc[gi] + (st.dt * Real(1.0 / 6.0)) * r;
-                st.u0[gi] = nu;
-                break;
+    // F: residual and RK stage per solution point; the new stage state
+    // replaces su for the traces
+#pragma unroll
+    for (int s = 0; s < NSPW; ++s) {
+        const int sp = lane + 32 * s;
+        if (sp >= NSP) break;
+        const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int k = v * NSP + sp;
+            const Real r = -sd[k] * iJ;
+            const int64_t gi = base + k;
+            Real u0v = Real(0), accv = Real(0);
+            if (st.stage >= 2) {
+                if constexpr (PREFETCH) {
+                    u0v = pu0[s][v];
+                    accv = pacc[s][v];
+                } else {
+                    u0v = st.u0[gi];
+                    accv = st.acc[gi];
+                }
+            }
+            Real nu;
+            switch (st.stage) {
+                case 0:
+                    st.R[gi] = r;
+                    nu = su[k];
+                    break;
+                case 1:
+                    st.acc[gi] = (st.dt * Real(1.0 / 6.0)) * r;
+                    nu = su[k] + (st.dt * Real(0.5)) * r;
+                    st.us[gi] = nu;
+                    break;
+                case 2:
+                    st.acc[gi] = accv + (st.dt * Real(1.0 / 3.0)) * r;
+                    nu = u0v + (st.dt * Real(0.5)) * r;
+                    st.us[gi] = nu;
+                    break;
+                case 3:
+                    st.acc[gi] = accv + (st.dt * Real(1.0 / 3.0)) * r;
+                    nu = u0v + st.dt * r;
+                    st.us[gi] = nu;
+                    break;
+                default:
+                    nu = u0v + accv + (st.dt * Real(1.0 / 6.0)) * r;
+                    st.u0[gi] = nu;
+                    break;
+            }
+            su[k] = nu;
         }
-        su[k] = nu;
     }
     if (st.uf_next) {
         __syncwarp();
@@ -855,7 +929,7 @@ __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t
             if (DIM == 3 && sp / (NP * NP) == j) w2 = double(op.w[j]);
         }
         double wt = w0 * w1 * w2;
-        wt *= double(g.J[e * g.sJ_e + sp * g.sJ_sp]);
+        wt *= double(g.J[e * g.sJ_e + sp * g.sJ_sp]);  // integrals use |J| itself
         const Real* ue = u + e * NV * NSP + sp;
         double m2 = 0.0;
 #pragma unroll
