@@ -267,12 +267,24 @@ __device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N,
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Per-element (per-warp) shared-memory footprint of each kernel, in Reals.
+// Regions (Reals) of one warp's shared memory.  F = NF*NV*NFP is one
+// element's face data, U = NV*NSP its state.
+//   visc : A su[U] | B sj[F] | C sl[F] | D sg[max(DIM*U, F)]  (D holds the
+//          staged neighbour traces during the face phase)
+//   resid: A su[U] | B sj[max(U,F)] (sd after the gradient) | C sc[F] |
+//          D sF[max(DIM*U, 2F)] (own + staged neighbour traces during the
+//          face phase) | E own + neighbour viscous fluxes [2F] (face phase)
 template <int DIM, int P>
 struct Smem {
     using Z = Sz<DIM, P>;
-    static constexpr int traces = Z::NV * Z::NSP;
-    static constexpr int visc = Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP;
-    static constexpr int resid = 2 * Z::NV * Z::NSP + 2 * Z::NF * Z::NV * Z::NFP + DIM * Z::NV * Z::NSP;
+    static constexpr int U = Z::NV * Z::NSP;
+    static constexpr int F = Z::NF * Z::NV * Z::NFP;
+    static constexpr int imax(int a, int b) { return a > b ? a : b; }
+    static constexpr int traces = U;
+    static constexpr int vB = U, vC = vB + F, vD = vC + F;
+    static constexpr int visc = vD + imax(DIM * U, F);
+    static constexpr int rB = U, rC = rB + imax(U, F), rD = rC + F, rE = rD + imax(DIM * U, 2 * F);
+    static constexpr int resid = rE + 2 * F;
 };
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
@@ -336,6 +348,33 @@ __device__ __forceinline__ void line_ends(const Real* sv, const Ops<Real>& op, i
     }
 }
 
+// ---- cp.async staging (global -> shared without registers)
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* s, const void* g) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// copy N Reals g -> s across the warp; 16-byte chunks when VEC (both sides
+// 16-byte aligned and N*sizeof(Real) a multiple of 16), else element-wise
+template <int N, bool VEC, typename Real>
+__device__ __forceinline__ void warp_stage(Real* s, const Real* g, int lane) {
+    if constexpr (VEC) {
+        constexpr int NC = int(N * sizeof(Real) / 16);
+        constexpr int RPC = int(16 / sizeof(Real));
+        for (int c = lane; c < NC; c += 32) cp_async16(s + c * RPC, g + c * RPC);
+    } else {
+        for (int c = lane; c < N; c += 32) cp_async_small<int(sizeof(Real))>(s + c, g + c);
+    }
+}
+
 // trace of variable v on face (d, side) at face point fp
 template <int DIM, int P, typename Real>
 __device__ __forceinline__ Real trace_of(const Real* sv, const Ops<Real>& op, int d, int side, int fp) {
@@ -395,14 +434,37 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (e >= E) return;
-    Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::visc;
-    Real* sj = su + NV * NSP;            // jumps u_c - u_f   [f][v][fp]
-    Real* sl = sj + NF * NV * NFP;       // own traces u_f    [f][v][fp]
-    Real* sg = sl + NF * NV * NFP;       // gradient          [d or i][v][sp]
-    warp_load<NV * NSP, Smem<DIM, P>::visc>(u + e * NV * NSP, su, lane);
+    using SM = Smem<DIM, P>;
+    Real* su = reinterpret_cast<Real*>(smem) + warp * SM::visc;
+    Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
+    Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
+    Real* sg = su + SM::vD;              // gradient          [d or i][v][sp]
+    Real* sn = sg;                       // staged neighbour traces [f][v][fp] (face phase only)
+    // face codes of this element, broadcast to every lane
+    int codes[NF];
+    {
+        const int mine = lane < NF ? g.nbr[e * NF + lane] : 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
+    }
+    // stage the element state and the neighbours' face traces (two groups)
+    constexpr bool VS = (SM::visc * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
+                        (SM::vD * sizeof(Real)) % 16 == 0;
+    constexpr bool VU = (SM::visc * sizeof(Real)) % 16 == 0 && (NV * NSP * sizeof(Real)) % 16 == 0;
+    if (VU && (reinterpret_cast<uintptr_t>(u + e * NV * NSP) & 15u) == 0)
+        warp_stage<NV * NSP, VU>(su, u + e * NV * NSP, lane);
+    else
+        warp_stage<NV * NSP, false>(su, u + e * NV * NSP, lane);
+    cp_async_commit();
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (codes[f] >= 0) warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
+    cp_async_commit();
+    cp_async_wait<1>();
     __syncwarp();
     // B: own traces (line pass), then neighbour traces and jumps per face point
     warp_write_traces<DIM, P>(su, sl, op, lane);
+    cp_async_wait<0>();
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -413,9 +475,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             Real uL[NV], uc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
-            const int code = g.nbr[e * NF + f];
+            const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             if (code >= 0) {
-                const Real* un = uf + int64_t(code >> 3) * NV * NFP;
+                const Real* un = sn + f * NV * NFP;
                 const int fpn = omap<DIM, NP>(code & 7, fp);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) uc[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]);
@@ -428,6 +490,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             for (int v = 0; v < NV; ++v) sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
         }
     }
+    __syncwarp();  // the gradient below overwrites the staged neighbour traces
     // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -507,7 +570,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             }
             Real N[DIM];
             load_normal<DIM>(g, e, f, fp, N);
-            const int code = g.nbr[e * NF + f];
+            const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             Real Fv[NV][DIM];
             if (code >= 0) {
                 visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
@@ -545,13 +608,40 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (e >= E) return;
-    Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::resid;
-    Real* sd = su + NV * NSP;            // divergence          [v][sp]
-    Real* sj = sd + NV * NSP;            // jumps u_c - u_f      [f][v][fp]
-    Real* sc = sj + NF * NV * NFP;       // Fc.N, then Fc.N - own [f][v][fp]
-    Real* sF = sc + NF * NV * NFP;       // own traces, q_d, then F~_d  [d][v][sp]
+    using SM = Smem<DIM, P>;
+    Real* su = reinterpret_cast<Real*>(smem) + warp * SM::resid;
+    Real* sj = su + SM::rB;              // jumps u_c - u_f      [f][v][fp]
+    Real* sd = sj;                       // divergence [v][sp], after the gradient
+    Real* sc = su + SM::rC;              // Fc.N, then Fc.N - own [f][v][fp]
+    Real* sF = su + SM::rD;              // own/neighbour traces, q_d, then F~_d  [d][v][sp]
+    Real* sl = sF;                       // own traces            [f][v][fp]  (face phase)
+    Real* sn = sF + NF * NV * NFP;       // neighbour traces      [f][v][fp]  (face phase)
+    Real* so = su + SM::rE;              // own viscous fluxes    [f][v][fp]  (face phase)
+    Real* sm = so + NF * NV * NFP;       // neighbour viscous fluxes [f][v][fp] (face phase)
     const int64_t base = e * NV * NSP;
-    warp_load<NV * NSP, Smem<DIM, P>::resid>(u + base, su, lane);
+    int codes[NF];
+    {
+        const int mine = lane < NF ? g.nbr[e * NF + lane] : 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
+    }
+    constexpr bool VS = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
+                        (SM::rD * sizeof(Real)) % 16 == 0 && (SM::rE * sizeof(Real)) % 16 == 0;
+    constexpr bool VU = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NSP * sizeof(Real)) % 16 == 0;
+    if (VU && (reinterpret_cast<uintptr_t>(u + base) & 15u) == 0)
+        warp_stage<NV * NSP, VU>(su, u + base, lane);
+    else
+        warp_stage<NV * NSP, false>(su, u + base, lane);
+    cp_async_commit();
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (codes[f] >= 0) {
+            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
+            if (ph.viscous)
+                warp_stage<NV * NFP, VS>(sm + f * NV * NFP, fvn + int64_t(codes[f] >> 3) * NV * NFP, lane);
+        }
+    if (ph.viscous) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane);
+    cp_async_commit();
     // the RK stage arrays are only needed at the end: issue their loads now
     Real pu0[NSPW][NV], pacc[NSPW][NV];
     if constexpr (PREFETCH) {
@@ -568,10 +658,11 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             }
         }
     }
+    cp_async_wait<1>();
     __syncwarp();
-    // B0: own traces of every face, one line pass (into the sF area)
-    Real* sl = sF;
+    // B0: own traces of every face, one line pass
     warp_write_traces<DIM, P>(su, sl, op, lane);
+    cp_async_wait<0>();
     __syncwarp();
     // B: common normal flux (Rusanov minus common viscous) and jumps
 #pragma unroll
@@ -585,13 +676,11 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
             Real N[DIM];
             load_normal<DIM>(g, e, f, fp, N);
-            const int code = g.nbr[e * NF + f];
-            int64_t nslot = 0;
+            const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             int fpn = 0;
             if (code >= 0) {
-                nslot = int64_t(code >> 3);
                 fpn = omap<DIM, NP>(code & 7, fp);
-                const Real* un = uf + nslot * NV * NFP;
+                const Real* un = sn + f * NV * NFP;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     uR[v] = un[v * NFP + fpn];
@@ -603,9 +692,9 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             Real Fc[NV];
             rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
             if (ph.viscous) {
-                const Real* own = fvn + (e * NF + f) * NV * NFP + fp;
+                const Real* own = so + f * NV * NFP + fp;
                 if (code >= 0) {
-                    const Real* nb = fvn + nslot * NV * NFP + fpn;
+                    const Real* nb = sm + f * NV * NFP + fpn;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) Fc[v] -= Real(0.5) * (own[v * NFP] - nb[v * NFP]);
                 } else {
