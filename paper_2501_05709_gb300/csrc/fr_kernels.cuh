@@ -271,9 +271,11 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // element's face data, U = NV*NSP its state.
 //   visc : A su[U] | B sj[F] | C sl[F] | D sg[max(DIM*U, F)]  (D holds the
 //          staged neighbour traces during the face phase)
-//   resid: A su[U] | B sj[max(U,F)] (sd after the gradient) | C sc[F] |
-//          D sF[max(DIM*U, 2F)] (own + staged neighbour traces during the
-//          face phase) | E own + neighbour viscous fluxes [2F] (face phase)
+//   resid: A su[U] | B sj[max(U,F)] (sd after the gradient) | C sc[F]
+//          (staged own viscous fluxes until each entry is replaced by the
+//          common flux of the same face point) | D sF[max(DIM*U, 2F)] (own +
+//          staged neighbour traces during the face phase) | E staged
+//          neighbour viscous fluxes [F] (face phase)
 template <int DIM, int P>
 struct Smem {
     using Z = Sz<DIM, P>;
@@ -284,7 +286,7 @@ struct Smem {
     static constexpr int vB = U, vC = vB + F, vD = vC + F;
     static constexpr int visc = vD + imax(DIM * U, F);
     static constexpr int rB = U, rC = rB + imax(U, F), rD = rC + F, rE = rD + imax(DIM * U, 2 * F);
-    static constexpr int resid = rE + 2 * F;
+    static constexpr int resid = rE + F;
 };
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
@@ -616,8 +618,8 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
     Real* sF = su + SM::rD;              // own/neighbour traces, q_d, then F~_d  [d][v][sp]
     Real* sl = sF;                       // own traces            [f][v][fp]  (face phase)
     Real* sn = sF + NF * NV * NFP;       // neighbour traces      [f][v][fp]  (face phase)
-    Real* so = su + SM::rE;              // own viscous fluxes    [f][v][fp]  (face phase)
-    Real* sm = so + NF * NV * NFP;       // neighbour viscous fluxes [f][v][fp] (face phase)
+    Real* so = sc;                       // own viscous fluxes    [f][v][fp]  (face phase)
+    Real* sm = su + SM::rE;              // neighbour viscous fluxes [f][v][fp] (face phase)
     const int64_t base = e * NV * NSP;
     int codes[NF];
     {
@@ -626,7 +628,8 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
     constexpr bool VS = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
-                        (SM::rD * sizeof(Real)) % 16 == 0 && (SM::rE * sizeof(Real)) % 16 == 0;
+                        (SM::rC * sizeof(Real)) % 16 == 0 && (SM::rD * sizeof(Real)) % 16 == 0 &&
+                        (SM::rE * sizeof(Real)) % 16 == 0;
     constexpr bool VU = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NSP * sizeof(Real)) % 16 == 0;
     if (VU && (reinterpret_cast<uintptr_t>(u + base) & 15u) == 0)
         warp_stage<NV * NSP, VU>(su, u + base, lane);

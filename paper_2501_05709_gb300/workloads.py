@@ -26,8 +26,9 @@ Workload recipes (paper Section 3.1 and Appendix C shapes):
 * ``box_mesh``: uniform periodic box, optionally curved by a smooth periodic
   displacement and/or with walls on the y faces.
 * ``ogrid_mesh``: spanwise-periodic O-grid of quadratic hexahedra around a
-  NACA 4-digit section (Section 3.4 parametrisation) or a circle, straight
-  radial rays to a circular far field, geometric radial stretching.
+  NACA 4-digit section (Section 3.4 parametrisation; surface nodes uniform in
+  arc length) or a circle, straight radial rays to a circular far field
+  centred at (0.5, 0), geometric radial stretching.
 * ``isentropic_vortex``, ``taylor_green``: closed-form flow fields.
 * ``perturbed_uniform``: free stream plus a seeded uniform velocity
   perturbation per solution point (PCG64).
@@ -197,7 +198,13 @@ def ogrid_mesh(n_theta, n_r, n_z, span, r_outer=10.0, first_cell=2e-3, body="nac
     beta = 2 * np.pi * np.arange(nt) / nt
     cx, cy = center
     if body == "naca":
-        xs, ys = naca4_surface(*naca, beta)
+        # surface nodes uniform in arc length (the cosine parameter alone
+        # would make trailing-edge cells orders of magnitude smaller)
+        fine = np.linspace(0.0, 2 * np.pi, 20001)
+        fx, fy = naca4_surface(*naca, fine)
+        arc = np.concatenate([[0.0], np.cumsum(np.hypot(np.diff(fx), np.diff(fy)))])
+        bq = np.interp(arc[-1] * np.arange(nt) / nt, arc, fine)
+        xs, ys = naca4_surface(*naca, bq)
     else:
         xs = cx + radius * np.cos(-beta)
         ys = cy + radius * np.sin(-beta)

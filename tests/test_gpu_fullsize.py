@@ -1,0 +1,162 @@
+"""Parity at the full workload sizes (TGV 32^3 p=3; NACA O-grid of 100,000
+quadratic hexahedra p=3), in the bench's launch configuration (autotuned
+tiles): sampled elements against the oracle, plus properties that hold at any
+size (discrete conservation), plus the batched multi-candidate context."""
+import math
+
+import numpy as np
+import pytest
+
+from ._cases import fp64_tol
+from ._subset import sampled_residual
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_05709_gb300 import build as B
+    B.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _tgv():
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = W.box_mesh(3, 32, 0.0, 2 * math.pi, q=1)
+    return nodes, conn
+
+
+def _solver(ph, p=3):
+    from oracle.fr import FRSolver
+    from oracle.mesh import Mesh
+
+    def make(n, c):
+        m = Mesh(n, c, p)
+        return m, FRSolver(m, ph)
+    return make
+
+
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 2e-3)])
+def test_tgv32_sampled_residual(precision, tol):
+    from oracle.physics import NavierStokes
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = _tgv()
+    p_inf = 1.0 / (1.4 * 0.01)
+    opts = F.options(order=3, precision=precision, viscous=True, mu=1 / 1600, p_inf=p_inf, dt=2.5e-4)
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        xsp = F.fr_sp_coords(ctx)
+        u = np.ascontiguousarray(np.moveaxis(W.taylor_green(xsp, mach=0.1), 0, 1))
+        F.fr_state_set(ctx, u)
+        F.fr_autotune(ctx)
+        dt = torch.float64 if precision == 0 else torch.float32
+        ud = torch.tensor(u, dtype=dt, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+    rng = np.random.default_rng(11)
+    sample = np.concatenate([[0, 31, 1023, 32767], rng.choice(32768, 40, replace=False)])
+    ph = NavierStokes(3, mu=1 / 1600)
+    make = _solver(ph)
+    Ro, ids = sampled_residual(make, nodes, conn, lambda ids, m: u[ids], sample)
+    if precision == 0:
+        from ._subset import submesh
+        sn, sc, sids, pos = submesh(nodes, conn, sample)
+        m, s = make(sn, sc)
+        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids])
+    assert _rel(R[ids], Ro) <= tol
+
+
+def test_tgv32_conservation_fp64():
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = _tgv()
+    opts = F.options(order=3, viscous=True, mu=1 / 1600, p_inf=1 / (1.4 * 0.01), dt=2.5e-4)
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        u = np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=0.1), 0, 1))
+        F.fr_state_set(ctx, u)
+        F.fr_autotune(ctx)
+        a = F.fr_integrals(ctx)
+        F.fr_rk_step_graph(ctx, 5)
+        b = F.fr_integrals(ctx)
+    assert np.all(np.abs(b[:5] - a[:5]) <= 1e-12 * np.abs(a[:5]).max())
+    assert b[5] < a[5]  # kinetic energy decays
+
+
+def _naca100k():
+    from paper_2501_05709_gb300 import workloads as W
+    return W.ogrid_mesh(250, 100, 4, 0.2, r_outer=10.0, first_cell=2e-3, body="naca", naca=(0.02, 0.4, 0.12))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-4)])
+def test_naca100k_sampled_residual(precision, tol):
+    from oracle.physics import NavierStokes
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = _naca100k()
+    rho, vel, p = W.freestream(0.2, 3.0)
+    opts = F.options(order=3, precision=precision, viscous=True, mu=1 / 23000, rho_inf=rho, p_inf=p,
+                     vel_inf=tuple(vel), dt=1e-5)
+    E = len(nodes)
+    u = W.perturbed_uniform(E, 64, rho, vel, p, amplitude=0.01, seed=0)
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        F.fr_autotune(ctx)
+        dt = torch.float64 if precision == 0 else torch.float32
+        ud = torch.tensor(u, dtype=dt, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+    # wall ring (trailing and leading edge), mid-field, far-field ring, spanwise seam
+    sample = np.array([0, 1, 125, 249, 250 * 50 + 7, 250 * 99 + 3, 250 * 99 + 249, 25000, 50125, 99999])
+    ph = NavierStokes(3, mu=1 / 23000, freestream=(rho, vel, p))
+    make = _solver(ph)
+    Ro, ids = sampled_residual(make, nodes, conn, lambda ids, m: u[ids], sample)
+    if precision == 0:
+        from ._subset import submesh
+        sn, sc, sids, pos = submesh(nodes, conn, sample)
+        m, s = make(sn, sc)
+        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids])
+    assert _rel(R[ids], Ro) <= tol
+
+
+def test_batched_candidates_match_separate_runs():
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    params = [(0.0, 0.4, 0.12, 16, 3), (0.04, 0.3, 0.10, 20, 4), (0.02, 0.5, 0.15, 12, 3)]
+    meshes = [W.ogrid_mesh(nt, nr, 2, 0.2, r_outer=4.0, first_cell=0.02, naca=(m, pc, t))
+              for m, pc, t, nt, nr in params]
+    rho, vel, p = W.freestream(0.2, 3.0)
+    a = math.radians(3.0)
+    opts = F.options(order=3, precision=1, viscous=True, mu=1 / 23000, rho_inf=rho, p_inf=p, vel_inf=tuple(vel),
+                     dt=2e-5, lift_dir=(-math.sin(a), math.cos(a), 0), drag_dir=(math.cos(a), math.sin(a), 0),
+                     ref_area=0.2)
+    states = [W.perturbed_uniform(len(n), 64, rho, vel, p, amplitude=0.01, seed=k) for k, (n, c) in enumerate(meshes)]
+    y, _, _ = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.1, span=0.2)
+    with F.fr_mesh_load(meshes, opts) as batch:
+        F.fr_state_set(batch, np.concatenate(states))
+        hs = [F.fwh_register(batch, k, y, 8) for k in range(3)]
+        F.fr_rk_step_graph(batch, 4)
+        ub = F.fr_state_get(batch)
+        fb = [F.fr_forces(batch, k) for k in range(3)]
+        hb = [F.fwh_history(batch, h, len(y)) for h in hs]
+    off = 0
+    for k, (n, c) in enumerate(meshes):
+        with F.fr_mesh_load((n, c), opts) as one:
+            F.fr_state_set(one, states[k])
+            h = F.fwh_register(one, 0, y, 8)
+            F.fr_rk_step(one, 4)
+            u1 = F.fr_state_get(one)
+            f1 = F.fr_forces(one, 0)
+            h1 = F.fwh_history(one, h, len(y))
+        assert np.array_equal(ub[off:off + len(n)], u1)
+        assert np.array_equal(fb[k], f1)
+        assert np.array_equal(hb[k], h1)
+        off += len(n)
