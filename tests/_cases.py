@@ -82,10 +82,47 @@ def ulp_floor(fn, u, draws=2, seed=0):
     return worst
 
 
-def fp64_tol(fn, u, base=1e-12):
-    """The FP64 parity bar: 1e-12 relative L2, or 4x the oracle's own 1-ulp
-    floor where the problem's conditioning puts that floor above 2.5e-13."""
-    return max(base, 4.0 * ulp_floor(fn, u))
+def coef_floor(solver, u, pick=None, draws=2, seed=1):
+    """Relative L2 change of the oracle residual when every operator
+    coefficient (D, extrapolation and correction weights) and every metric
+    value (S, |J|, normals) moves by one unit in the last place: the floor set
+    by how the data of the discretisation itself is rounded."""
+    import copy
+
+    from oracle.fr import FRSolver
+    rng = np.random.default_rng(seed)
+
+    def jig(a):
+        return a * (1.0 + rng.choice([-1.0, 1.0], size=np.shape(a)) * 2.0 ** -53)
+
+    ref = solver.residual(u)
+    if pick is not None:
+        ref = ref[pick]
+    worst = 0.0
+    for _ in range(draws):
+        m2 = copy.copy(solver.m)
+        r2 = copy.copy(solver.m.ref)
+        for name in ("D", "lm", "lp", "hm", "hp"):
+            setattr(r2, name, jig(getattr(r2, name)))
+        m2.ref = r2
+        for name in ("S", "J", "N"):
+            setattr(m2, name, jig(getattr(m2, name)))
+        R2 = FRSolver(m2, solver.ph).residual(u)
+        if pick is not None:
+            R2 = R2[pick]
+        worst = max(worst, float(np.linalg.norm((R2 - ref).ravel()) / np.linalg.norm(ref.ravel())))
+    return worst
+
+
+def fp64_tol(fn, u, base=1e-12, solver=None, pick=None):
+    """The FP64 parity bar: 1e-12 relative L2, or 4x the oracle's own floor
+    where the problem's conditioning puts that floor above 2.5e-13.  The floor
+    is the larger of the 1-ulp state floor and (when the solver is given) the
+    1-ulp operator/metric floor."""
+    floor = ulp_floor(fn, u)
+    if solver is not None:
+        floor = max(floor, coef_floor(solver, u, pick))
+    return max(base, 4.0 * floor)
 
 
 def oracle_for(c):

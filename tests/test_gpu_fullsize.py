@@ -42,8 +42,17 @@ def _solver(ph, p=3):
     return make
 
 
-@pytest.mark.parametrize("precision,tol", [(0, None), (1, 2e-3)])
-def test_tgv32_sampled_residual(precision, tol):
+# Three states at the full 32^3 size in the bench's launch configuration:
+#  "smooth": a random smooth state (residual of the size of the fluxes), FP64
+#            under the plain 1e-12 bar -- the detector for indexing/tile bugs;
+#  "tgv":    the Taylor-Green initial state, whose residual (~1e-4..1e-2) is a
+#            small difference of fluxes carrying p ~ 71: FP64 is bounded by 16x
+#            the oracle's measured 1-ulp floors (state and operator data);
+#  FP32 on "tgv": float rounding of those fluxes alone gives a percent-level
+#            relative residual error, while the FP32 state stays within ~1e-6
+#            of FP64 over hundreds of steps (next test).
+@pytest.mark.parametrize("state,precision,tol", [("smooth", 0, None), ("tgv", 0, None), ("tgv", 1, 5e-2)])
+def test_tgv32_sampled_residual(state, precision, tol):
     from oracle.physics import NavierStokes
     from paper_2501_05709_gb300 import fr as F
     from paper_2501_05709_gb300 import workloads as W
@@ -52,7 +61,11 @@ def test_tgv32_sampled_residual(precision, tol):
     opts = F.options(order=3, precision=precision, viscous=True, mu=1 / 1600, p_inf=p_inf, dt=2.5e-4)
     with F.fr_mesh_load((nodes, conn), opts) as ctx:
         xsp = F.fr_sp_coords(ctx)
-        u = np.ascontiguousarray(np.moveaxis(W.taylor_green(xsp, mach=0.1), 0, 1))
+        if state == "tgv":
+            u = np.ascontiguousarray(np.moveaxis(W.taylor_green(xsp, mach=0.1), 0, 1))
+        else:
+            u = np.ascontiguousarray(np.moveaxis(W.random_smooth_state(xsp, seed=4, periods=[2 * math.pi] * 3),
+                                                 0, 1))
         F.fr_state_set(ctx, u)
         F.fr_autotune(ctx)
         dt = torch.float64 if precision == 0 else torch.float32
@@ -67,11 +80,34 @@ def test_tgv32_sampled_residual(precision, tol):
     make = _solver(ph)
     Ro, ids = sampled_residual(make, nodes, conn, lambda ids, m: u[ids], sample)
     if precision == 0:
+        from ._cases import coef_floor, ulp_floor
         from ._subset import submesh
         sn, sc, sids, pos = submesh(nodes, conn, sample)
         m, s = make(sn, sc)
-        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids])
+        if state == "smooth":
+            tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids], solver=s, pick=pos)
+        else:
+            floor = max(ulp_floor(lambda v: s.residual(v)[pos], u[sids]), coef_floor(s, u[sids], pos))
+            tol = 16.0 * floor
     assert _rel(R[ids], Ro) <= tol
+
+
+def test_tgv32_fp32_state_tracks_fp64():
+    # the FP32 state after 40 RK4 steps stays within 2e-6 (relative L2) of FP64
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, conn = _tgv()
+    out = []
+    for prec in (0, 1):
+        opts = F.options(order=3, precision=prec, viscous=True, mu=1 / 1600, p_inf=1 / (1.4 * 0.01), dt=2.5e-4)
+        with F.fr_mesh_load((nodes, conn), opts) as ctx:
+            u = np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=0.1), 0, 1))
+            F.fr_state_set(ctx, u)
+            F.fr_rk_step_graph(ctx, 40)
+            out.append((F.fr_state_get(ctx), F.fr_integrals(ctx)))
+    (u64, i64), (u32, i32) = out
+    assert _rel(u32, u64) <= 2e-6
+    assert abs(i32[5] - i64[5]) <= 1e-5 * abs(i64[5])   # kinetic energy
 
 
 def test_tgv32_conservation_fp64():
@@ -123,7 +159,7 @@ def test_naca100k_sampled_residual(precision, tol):
         from ._subset import submesh
         sn, sc, sids, pos = submesh(nodes, conn, sample)
         m, s = make(sn, sc)
-        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids])
+        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids], solver=s, pick=pos)
     assert _rel(R[ids], Ro) <= tol
 
 
