@@ -17,9 +17,13 @@ HUYNH_G2 = 1
 
 
 def gauss_legendre(n):
-    """n GL points and weights on [-1, 1] (library primitive)."""
+    """n GL points and weights on [-1, 1] (library primitive), made exactly
+    symmetric about 0: P_n has definite parity, so its roots come in +-
+    pairs (and 0 for odd n) and the weights pair up equally."""
     x, w = npleg.leggauss(n)
-    return np.asarray(x, float), np.asarray(w, float)
+    x = 0.5 * (np.asarray(x, float) - np.asarray(x, float)[::-1])
+    w = 0.5 * (np.asarray(w, float) + np.asarray(w, float)[::-1])
+    return x, w
 
 
 def gauss_lobatto(n):

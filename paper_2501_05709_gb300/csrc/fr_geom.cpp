@@ -33,6 +33,17 @@ void gauss_legendre(int n, double* x, double* w) {
         x[n - 1 - i] = z;
         w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dP[n] * dP[n]);
     }
+    // P_n has definite parity: the roots pair as +-x (0 for odd n) with equal
+    // weights; impose it exactly so mirrored operators are bit-symmetric
+    for (int i = 0; i < n / 2; ++i) {
+        const double a = 0.5 * (x[n - 1 - i] - x[i]);
+        const double b = 0.5 * (w[n - 1 - i] + w[i]);
+        x[n - 1 - i] = a;
+        x[i] = -a;
+        w[n - 1 - i] = b;
+        w[i] = b;
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
 void gauss_lobatto(int n, double* x) {
