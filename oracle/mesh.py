@@ -95,23 +95,31 @@ class Mesh:
         # nodal coordinates as tensors [E, dim(comp), (q+1)...]
         X = nodes.reshape((E,) + (q + 1,) * dim + (dim,))
         X = np.moveaxis(X, -1, 1)
+        # Derivatives of the map and the conservative-curl products use
+        # coordinates relative to the element's node centroid: both are
+        # invariant under a translation (sum_a l_a' = 0, and the curl of
+        # c grad x_m vanishes when the map lies in the interpolation space,
+        # q <= p), and the relative coordinates avoid cancellation in
+        # elements far from the origin.
+        cen = nodes.mean(axis=1)                         # [E, dim]
+        Xr = X - cen.reshape((E, dim) + (1,) * dim)
 
-        def geo(pts, deriv=None):
+        def geo(pts, deriv=None, rel=False):
             mats = [lagrange(xe, pts[d]) if deriv != d else lagrange_deriv(xe, pts[d])
                     for d in range(dim)]
-            return _apply(X, mats, dim)
+            return _apply(Xr if rel else X, mats, dim)
 
         gl = [ref.x] * dim
         self.xsp = np.moveaxis(geo(gl), 1, -1).reshape(E, -1, dim)
-        A = np.stack([geo(gl, k) for k in range(dim)], axis=2)  # [E, comp i, deriv k, ...]
+        A = np.stack([geo(gl, k, rel=True) for k in range(dim)], axis=2)  # [E, comp i, deriv k, ...]
         A = A.reshape(E, dim, dim, -1)
         self.J = np.linalg.det(np.moveaxis(A, -1, 1))  # [E, Nsp]
         if np.any(self.J <= 0.0):
             raise ValueError("non-positive Jacobian")
         # GLL values of the map and its derivatives (exact from the map)
         gll = [ref.gll] * dim
-        xg = geo(gll)                                   # [E, i, gll...]
-        ag = np.stack([geo(gll, k) for k in range(dim)], axis=2)  # [E, i, k, gll...]
+        xg = geo(gll, rel=True)                         # [E, i, gll...] (relative)
+        ag = np.stack([geo(gll, k, rel=True) for k in range(dim)], axis=2)  # [E, i, k, gll...]
 
         def smetric(pts):
             """S[E, d, i, ...] evaluated on the tensor grid pts (list of 1D arrays)."""

@@ -213,9 +213,21 @@ void element_geometry(int dim, int q, const Ref1D& r, const double* nodes, doubl
     basis_mat(xe, nq, r.gll, n, true, Edgll);
     basis_mat(xe, nq, r.x, n, false, Egl);
     basis_mat(xe, nq, r.x, n, true, Edgl);
-    // node components padded into [nq]^dim layout; apply with [n][nq] matrices.
-    // tensor_apply wants square inputs of size n, so pad the nodes to n^dim.
-    auto map_eval = [&](int comp, const double* M0, const double* M1, const double* M2, double* out) {
+    // Derivatives of the map and the curl-form products are evaluated from
+    // node coordinates relative to the node centroid: a translation changes
+    // neither (the Lagrange derivative weights sum to zero; the curl of
+    // c grad x_m vanishes for maps inside the interpolation space), and it
+    // removes cancellation in elements far from the origin.
+    const int nn = (dim == 2) ? nq * nq : nq * nq * nq;
+    double cen[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < nn; ++a)
+        for (int c = 0; c < dim; ++c) cen[c] += nodes[a * dim + c];
+    for (int c = 0; c < dim; ++c) cen[c] /= nn;
+    double rnodes[27 * 3];
+    for (int a = 0; a < nn; ++a)
+        for (int c = 0; c < dim; ++c) rnodes[a * dim + c] = nodes[a * dim + c] - cen[c];
+    auto map_eval_of = [&](const double* nd, int comp, const double* M0, const double* M1, const double* M2,
+                           double* out) {
         // in: nq^dim node values; matrices [n][nq]; do explicit loops
         if (dim == 2) {
             for (int b2 = 0; b2 < n; ++b2)
@@ -223,7 +235,7 @@ void element_geometry(int dim, int q, const Ref1D& r, const double* nodes, doubl
                     double s = 0;
                     for (int b = 0; b < nq; ++b)
                         for (int a = 0; a < nq; ++a)
-                            s += M1[b2 * nq + b] * M0[a2 * nq + a] * nodes[(b * nq + a) * dim + comp];
+                            s += M1[b2 * nq + b] * M0[a2 * nq + a] * nd[(b * nq + a) * dim + comp];
                     out[b2 * n + a2] = s;
                 }
             return;
@@ -236,7 +248,7 @@ void element_geometry(int dim, int q, const Ref1D& r, const double* nodes, doubl
                         for (int b = 0; b < nq; ++b)
                             for (int a = 0; a < nq; ++a)
                                 s += M2[c2 * nq + c] * M1[b2 * nq + b] * M0[a2 * nq + a] *
-                                     nodes[((c * nq + b) * nq + a) * dim + comp];
+                                     nd[((c * nq + b) * nq + a) * dim + comp];
                     out[(c2 * n + b2) * n + a2] = s;
                 }
     };
@@ -244,9 +256,9 @@ void element_geometry(int dim, int q, const Ref1D& r, const double* nodes, doubl
     double X[3][MAXNP * MAXNP * MAXNP];
     double A[3][3][MAXNP * MAXNP * MAXNP];  // A[c][k] = dx_c/dxi_k at GL points
     for (int c = 0; c < dim; ++c) {
-        map_eval(c, Egl, Egl, Egl, X[c]);
+        map_eval_of(nodes, c, Egl, Egl, Egl, X[c]);
         for (int k = 0; k < dim; ++k)
-            map_eval(c, k == 0 ? Edgl : Egl, k == 1 ? Edgl : Egl, k == 2 ? Edgl : Egl, A[c][k]);
+            map_eval_of(rnodes, c, k == 0 ? Edgl : Egl, k == 1 ? Edgl : Egl, k == 2 ? Edgl : Egl, A[c][k]);
     }
     for (int s = 0; s < nsp; ++s) {
         for (int c = 0; c < dim; ++c) xsp[s * dim + c] = X[c][s];
@@ -263,9 +275,9 @@ void element_geometry(int dim, int q, const Ref1D& r, const double* nodes, doubl
     double xg[3][MAXNP * MAXNP * MAXNP];
     double ag[3][3][MAXNP * MAXNP * MAXNP];
     for (int c = 0; c < dim; ++c) {
-        map_eval(c, Egll, Egll, Egll, xg[c]);
+        map_eval_of(rnodes, c, Egll, Egll, Egll, xg[c]);
         for (int k = 0; k < dim; ++k)
-            map_eval(c, k == 0 ? Edgll : Egll, k == 1 ? Edgll : Egll, k == 2 ? Edgll : Egll, ag[c][k]);
+            map_eval_of(rnodes, c, k == 0 ? Edgll : Egll, k == 1 ? Edgll : Egll, k == 2 ? Edgll : Egll, ag[c][k]);
     }
     // evaluation of GLL-interpolated fields (and one derivative) on target grids
     double Igl[MAXNP * MAXNP], Dgl[MAXNP * MAXNP];   // GLL -> GL
