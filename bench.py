@@ -23,6 +23,8 @@ from __future__ import annotations
 import argparse
 import json
 import math
+
+import numpy as np
 import os
 import subprocess
 import sys
@@ -125,14 +127,18 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def algorithmic_bytes(E, p, rsz, viscous=True, dim=3):
-    """Minimum HBM bytes per RK stage of each kernel (affine mesh): every array
-    the kernel must touch, read or written once."""
+def algorithmic_bytes(E, p, rsz, viscous=True, dim=3, curved=False):
+    """Minimum HBM bytes per RK stage of each kernel: every array the kernel
+    must touch, read or written once.  Metrics: one set per element (affine)
+    or S and 1/|J| per solution point and a normal per flux point (curved)."""
     np_ = p + 1
     nsp, nfp, nf, nv = np_ ** dim, np_ ** (dim - 1), 2 * dim, dim + 2
     u = nv * nsp * rsz
     tr = nf * nv * nfp * rsz
-    geo = (dim * dim + 1 + nf * dim) * rsz + nf * 4
+    if curved:
+        geo = (dim * dim + 1) * nsp * rsz + nf * nfp * dim * rsz + nf * 4
+    else:
+        geo = (dim * dim + 1 + nf * dim) * rsz + nf * 4
     traces = E * (u + tr)
     visc = E * (u + tr + tr + geo) if viscous else 0
     rk = (2 + 4 + 4 + 3) / 4.0 * u
@@ -140,6 +146,59 @@ def algorithmic_bytes(E, p, rsz, viscous=True, dim=3):
     # RK stage arrays (stage-averaged) and the traces of the updated state
     resid = E * (u + tr + (2 * tr if viscous else 0) + geo + rk + tr)
     return {"traces": traces, "visc": visc, "resid": resid}
+
+
+WORKLOADS = {
+    "tgv32_p3": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, FR p=3 (2,097,152 DOF), "
+                "Rusanov+BR2, RK4 dt=2.5e-4",
+    "tgv32_p4": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, FR p=4 (4,096,000 DOF), "
+                "Rusanov+BR2, RK4 dt=1.5e-4",
+    "naca100k_p3": "NACA 2412 (m=0.02, p=0.4, t=0.12) spanwise-periodic O-grid, 250x100x4 = 100,000 quadratic "
+                   "hexes, span 0.2c, FR p=3 (6,400,000 DOF), Re=23000, M=0.2, AoA 3 deg, 1% seeded noise, "
+                   "RK4 dt=3e-6, wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled every step",
+    "batch12_p3": "12 NACA 4-digit candidates (PCG64 seed 1: m~U[0,0.06], p~U[0.2,0.6], t~U[0.08,0.16], "
+                  "20k-80k quadratic hexes each, 599,888 in total, 38.4M DOF) in one context, FR p=3, Re=23000, "
+                  "M=0.2, AoA 3 deg, RK4 dt=3e-6, forces and one FW-H cylinder per candidate every step",
+}
+
+
+def build_workload(name):
+    """(meshes, options(prec), initial state(ctx), surfaces per candidate, curved flag)."""
+    from paper_2501_05709_gb300 import cases as C
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    if name.startswith("tgv32"):
+        p = 3 if name.endswith("p3") else 4
+        dt = 2.5e-4 if p == 3 else 1.5e-4
+        nodes, conn = W.box_mesh(3, 32, 0.0, 2 * math.pi, q=1)
+        p_inf = 1.0 / (GAMMA * MACH ** 2)
+
+        def opts(prec):
+            return F.options(order=p, precision=prec, viscous=True, mu=1.0 / 1600.0, p_inf=p_inf, dt=dt)
+
+        def state(ctx):
+            return np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=MACH), 0, 1))
+        return [(nodes, conn)], opts, state, [], False
+    if name == "naca100k_p3":
+        params = [{"naca": (0.02, 0.4, 0.12), "n_theta": 250, "n_r": 100}]
+    elif name == "batch12_p3":
+        params = C.batch_params(12, seed=1)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    meshes, free, o32 = [], None, None
+    for prm in params:
+        nodes, conn, _, free = C.naca_setup(naca=prm["naca"], n_theta=prm["n_theta"], n_r=prm["n_r"])
+        meshes.append((nodes, conn))
+    rho, vel, pinf = free
+
+    def opts(prec):
+        return C.naca_setup(n_theta=2, n_r=1, n_z=1, precision=prec, dt=3e-6)[2]
+
+    def state(ctx):
+        return np.concatenate([W.perturbed_uniform(len(n), ctx.nsp, rho, vel, pinf, amplitude=0.01, seed=k)
+                               for k, (n, _) in enumerate(meshes)])
+    surf = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=0.2)[0]
+    return meshes, opts, state, [surf] * len(meshes), True
 
 
 def gpu_leg(args, rank, world, local_rank):
@@ -152,23 +211,20 @@ def gpu_leg(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     B.build()
-    n, p = 32, 3
-    nodes, conn = W.box_mesh(3, n, 0.0, 2 * math.pi, q=1)
-    p_inf = 1.0 / (GAMMA * MACH ** 2)
-
-    def opts(prec):
-        return F.options(order=p, precision=prec, viscous=True, mu=1.0 / 1600.0, p_inf=p_inf, dt=DT)
-
+    meshes, opts, state_of, surfaces, curved = build_workload(args.workload)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     prec = F.FR_FP32 if args.precision == "fp32" else F.FR_FP64
     rsz = 4 if prec == F.FR_FP32 else 8
-    ctx = F.fr_mesh_load((nodes, conn), opts(prec))
-    xsp = F.fr_sp_coords(ctx)
-    u0 = np.ascontiguousarray(np.moveaxis(W.taylor_green(xsp, mach=MACH), 0, 1))
+    ctx = F.fr_mesh_load(meshes, opts(prec))
+    p = ctx.order
+    u0 = state_of(ctx)
     E, nsp = ctx.nelem, ctx.nsp
     dof = E * nsp
     F.fr_state_set(ctx, u0)
+    cap = args.warmup + 3 * args.steps + 8
+    for k, srf in enumerate(surfaces):
+        F.fwh_register(ctx, k, srf, cap, 1)
     if args.tile > 0:
         F.fr_set_tile(ctx, args.tile)
         tile = args.tile
@@ -208,7 +264,7 @@ def gpu_leg(args, rank, world, local_rank):
     # per-kernel durations of the same steps, events around each launch
     kms, kn = F.fr_profile_step(ctx, args.steps, sh)
     hbm, peak_kind = peaks()
-    ab = algorithmic_bytes(E, p, rsz)
+    ab = algorithmic_bytes(E, p, rsz, curved=curved)
     resid_ms = kms[2] / max(kn[2], 1)
     achieved = ab["resid"] / (resid_ms / 1e3) / 1e9
     def kstat(i, key):
@@ -243,8 +299,10 @@ def gpu_leg(args, rank, world, local_rank):
     # FP64 path, same workload, same number of steps
     fp64 = None
     if not args.no_fp64 and prec == F.FR_FP32:
-        c64 = F.fr_mesh_load((nodes, conn), opts(F.FR_FP64))
+        c64 = F.fr_mesh_load(meshes, opts(F.FR_FP64))
         F.fr_state_set(c64, u0)
+        for k, srf in enumerate(surfaces):
+            F.fwh_register(c64, k, srf, cap, 1)
         if args.tile > 0:
             F.fr_set_tile(c64, args.tile)
         else:
@@ -286,15 +344,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
+    ap.add_argument("--workload", default="tgv32_p3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the timed path (fp32 also times fp64 beside it)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    config = {"workload": "tgv32_p3", "description": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, "
-              "FR p=3 (2,097,152 DOF), Rusanov+BR2, RK4 dt=2.5e-4", "elements": 32768, "order": 3,
-              "dof_per_variable": 2097152, "step": "one RK4 step = 4 residual stages",
+    config = {"workload": args.workload, "description": WORKLOADS[args.workload],
+              "step": "one RK4 step = 4 residual stages (fused stage updates; forces and FW-H sampling "
+                      "every step where the workload has walls/surfaces)",
               "l2": "working set larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"}
 
     if args.impl == "reference":
@@ -323,6 +382,8 @@ def main():
             except Exception as e:  # reported, not fatal
                 cb = {"value": None, "error": str(e)[-300:]}
         config["autotuned_elements_per_block"] = r["tile_epb"]
+        config["elements"] = r["elements"]
+        config["dof_per_variable"] = r["dof"]
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",

@@ -161,12 +161,15 @@ int fr_forces_reset(fr_ctx* ctx);
  * Taylor-Green kinetic-energy history. */
 int fr_integrals(fr_ctx* ctx, int cand, double* out);
 
-/* fwh_register (Section 3.1 permeable data surface): locates npts physical
- * points xyz (host double [npts][3]) in candidate cand by Newton inversion of
- * the element maps (lowest element id wins on shared faces) and reserves a
- * device history of capacity records.  *handle identifies the surface.
- * Errors: FR_EINVAL (point outside the mesh, bad sizes), FR_ENOMEM. */
-int fwh_register(fr_ctx* ctx, int cand, int npts, const double* xyz, int capacity, int* handle);
+/* fwh_register (Section 3.1 permeable data surface; the paper collects every
+ * 25 steps): locates npts physical points xyz (host double [npts][3]) in
+ * candidate cand by Newton inversion of the element maps (lowest element id
+ * wins on shared faces) and reserves a device history of capacity records.
+ * fr_rk_step appends a record at the start of every `every`-th step (every
+ * >= 1; the step counter is kept on the device, so graph replays stay in
+ * phase).  *handle identifies the surface.  Errors: FR_EINVAL (point outside
+ * the mesh, bad sizes), FR_ENOMEM. */
+int fwh_register(fr_ctx* ctx, int cand, int npts, const double* xyz, int capacity, int every, int* handle);
 
 /* fwh_sample: appends one record of (rho, V_1..V_3, p) at every point of
  * surface handle from the current state (FR_EINVAL when full).  Records are

@@ -1,0 +1,167 @@
+"""Drivers for the airfoil workloads on the C-ABI: one NACA 4-digit candidate
+(mean lift/drag, FW-H surface samples, OASPL at a far-field observer) and a
+batch of candidates advanced together in one context, as one MADS poll does
+(paper Section 2.2 and Section 3.4: 2n candidates evaluated concurrently).
+
+Everything numerical runs in libfr; this module only builds inputs, calls the
+library and reduces its outputs.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import fr as F
+from . import workloads as W
+
+GAMMA = 1.4
+
+
+def naca_setup(naca=(0.02, 0.4, 0.12), n_theta=250, n_r=100, n_z=4, span=0.2, r_outer=10.0, first_cell=2e-3,
+               mach=0.2, aoa_deg=3.0, reynolds=23000.0, order=3, precision=F.FR_FP32, dt=3e-6):
+    """Mesh (quadratic O-grid), options and free stream of one candidate."""
+    nodes, conn = W.ogrid_mesh(n_theta, n_r, n_z, span, r_outer=r_outer, first_cell=first_cell, body="naca",
+                               naca=naca)
+    rho, vel, p = W.freestream(mach, aoa_deg)
+    a = math.radians(aoa_deg)
+    opts = F.options(order=order, precision=precision, viscous=True, mu=rho * 1.0 * 1.0 / reynolds,
+                     rho_inf=rho, p_inf=p, vel_inf=tuple(vel), dt=dt,
+                     lift_dir=(-math.sin(a), math.cos(a), 0.0), drag_dir=(math.cos(a), math.sin(a), 0.0),
+                     ref_area=1.0 * span)
+    return nodes, conn, opts, (rho, vel, p)
+
+
+def oaspl_from_history(hist, surface, dtau, observer, free, mach_vec, span, ncopies, stream=None):
+    """FW-H (libfr fwh_integrate) of a history [nrec, npts, 5] -> (t*, p', p'_rms,
+    OASPL in dB re 20 uPa with p_inf scaled to 101325 Pa), or raises FrError
+    (FR_EWINDOW) when the record is too short for the observer window."""
+    import torch
+    rho, vel, p = free
+    c0 = math.sqrt(GAMMA * p / rho)
+    y, n, dS = surface
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    pout, nt, t0 = F.fwh_integrate(dev(hist), dev(y), dev(n), dev(dS), dtau, 0.0, np.asarray(observer)[None],
+                                   mach_vec, c0, rho, p, Lspan=span, ncopies=ncopies, stream=stream)
+    pp = pout[0, :nt[0]].cpu().numpy()
+    prms = float(np.sqrt(np.mean((pp - pp.mean()) ** 2)))
+    oaspl = 20.0 * math.log10(max(prms, 1e-300) * (101325.0 / p) / 2e-5)
+    return t0[0] + dtau * np.arange(nt[0]), pp, prms, oaspl
+
+
+def run_naca(steps=2000, precision=F.FR_FP32, sample_every=1, ncopies=1, observer=(1.0, -10.0, 0.1),
+             surface_radius=1.5, seed=0, graph=True, **mesh_kw):
+    """One candidate: perturbed free stream (1% seeded velocity noise), `steps`
+    RK4 steps, forces every step, the FW-H surface sampled every
+    `sample_every` steps, then FW-H at the observer.  Returns a dict."""
+    nodes, conn, opts, free = naca_setup(precision=precision, **mesh_kw)
+    span = mesh_kw.get("span", 0.2)
+    rho, vel, p = free
+    surface = W.cylinder_surface(radius=surface_radius, center=(0.5, 0.0), spacing=0.01, span=span)
+    out = {"elements": len(nodes), "steps": steps, "precision": "fp32" if precision == F.FR_FP32 else "fp64"}
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        u0 = W.perturbed_uniform(ctx.nelem, ctx.nsp, rho, vel, p, amplitude=0.01, seed=seed)
+        F.fr_state_set(ctx, u0)
+        cap = (steps + sample_every - 1) // sample_every
+        h = F.fwh_register(ctx, 0, surface[0], cap, sample_every)
+        import torch
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        (F.fr_rk_step_graph if graph else F.fr_rk_step)(ctx, steps)
+        torch.cuda.synchronize()
+        out["seconds"] = time.perf_counter() - t
+        out["dof_stages_per_s"] = ctx.nelem * ctx.nsp * 4 * steps / out["seconds"]
+        f = F.fr_forces(ctx, 0)
+        out.update(cl=f[0], cd=f[1], cl_mean=f[2], cd_mean=f[3], force_steps=int(f[4]))
+        hist = F.fwh_history(ctx, h, len(surface[0]))
+        out["records"] = hist.shape[0]
+        final = F.fr_state_get(ctx)
+        out["finite"] = bool(np.isfinite(final).all())
+    c0 = math.sqrt(GAMMA * p / rho)
+    mach_vec = np.asarray(vel) / c0
+    try:
+        _, pp, prms, oaspl = oaspl_from_history(hist, surface, opts.dt * sample_every, observer, free, mach_vec,
+                                                span, ncopies)
+        out.update(prms=prms, oaspl_db=oaspl, window=len(pp))
+    except F.FrError as e:
+        out.update(prms=None, oaspl_db=None, window=0, fwh_error=str(e))
+    out["history"] = hist
+    return out
+
+
+def batch_params(n=12, seed=1):
+    """Seeded MADS-poll candidates: camber m ~ U[0, 0.06], its position
+    p ~ U[0.2, 0.6], thickness t ~ U[0.08, 0.16], element count ~ U[20k, 80k]
+    realised as n_theta x n_r x 4 with n_r = 2 n_theta / 5."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        m = rng.uniform(0.0, 0.06)
+        pc = rng.uniform(0.2, 0.6)
+        t = rng.uniform(0.08, 0.16)
+        ne = rng.uniform(20000, 80000)
+        nt = int(round(math.sqrt(ne / 4 * 5 / 2)))
+        nr = max(4, int(round(ne / 4 / nt)))
+        out.append({"naca": (m, pc, t), "n_theta": nt, "n_r": nr})
+    return out
+
+
+def run_batch(params, steps, precision=F.FR_FP32, dt=3e-6, sample_every=1, surface_radius=1.5, seed=0,
+              graph=True):
+    """All candidates in one context (concatenated elements; one graph-replayed
+    launch sequence per RK4 step).  Returns per-candidate mean C_L, C_D, the
+    histories and the throughput."""
+    import torch
+    meshes, frees, opts = [], None, None
+    for k, prm in enumerate(params):
+        nodes, conn, o, free = naca_setup(naca=prm["naca"], n_theta=prm["n_theta"], n_r=prm["n_r"],
+                                         precision=precision, dt=dt)
+        meshes.append((nodes, conn))
+        frees, opts = free, o
+    rho, vel, p = frees
+    surface = W.cylinder_surface(radius=surface_radius, center=(0.5, 0.0), spacing=0.01, span=0.2)
+    res = {"candidates": len(params), "elements": [len(n) for n, _ in meshes], "steps": steps}
+    with F.fr_mesh_load(meshes, opts) as ctx:
+        us = [W.perturbed_uniform(len(n), ctx.nsp, rho, vel, p, amplitude=0.01, seed=seed + k)
+              for k, (n, _) in enumerate(meshes)]
+        F.fr_state_set(ctx, np.concatenate(us))
+        cap = (steps + sample_every - 1) // sample_every
+        hs = [F.fwh_register(ctx, k, surface[0], cap, sample_every) for k in range(len(meshes))]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        (F.fr_rk_step_graph if graph else F.fr_rk_step)(ctx, steps)
+        torch.cuda.synchronize()
+        res["seconds"] = time.perf_counter() - t
+        res["dof_stages_per_s"] = ctx.nelem * ctx.nsp * 4 * steps / res["seconds"]
+        res["forces"] = [F.fr_forces(ctx, k) for k in range(len(meshes))]
+        res["histories"] = [F.fwh_history(ctx, h, len(surface[0])) for h in hs]
+    return res
+
+
+def precision_study(steps=25000, dt=4e-5, sample_every=4, n_theta=60, n_r=20, n_z=2, first_cell=2e-2):
+    """Mean C_L, C_D and OASPL of one NACA 2412 candidate in FP32 and FP64 on a
+    coarse O-grid run for steps*dt convective times (long enough for a
+    non-empty FW-H window at the observer 10c below the trailing edge)."""
+    out = {}
+    for prec, name in ((F.FR_FP64, "fp64"), (F.FR_FP32, "fp32")):
+        r = run_naca(steps=steps, precision=prec, sample_every=sample_every, dt=dt, n_theta=n_theta, n_r=n_r,
+                     n_z=n_z, first_cell=first_cell)
+        r.pop("history")
+        out[name] = r
+    d = {}
+    for key in ("cl_mean", "cd_mean", "oaspl_db", "prms"):
+        a, b = out["fp64"].get(key), out["fp32"].get(key)
+        if a is not None and b is not None:
+            d[key] = {"fp64": a, "fp32": b, "abs_dev": abs(b - a), "rel_dev": abs(b - a) / max(abs(a), 1e-300)}
+    out["deviation"] = d
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "naca-precision":
+        print(json.dumps(precision_study(), default=float))
+    else:
+        print("usage: python -m paper_2501_05709_gb300.cases naca-precision")

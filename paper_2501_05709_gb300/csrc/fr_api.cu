@@ -37,12 +37,11 @@ static int fail(int code, const std::string& msg) {
 namespace {
 
 struct Surface {
-    int cand = 0, npts = 0, cap = 0;
+    int cand = 0, npts = 0, cap = 0, every = 1;
     int64_t* pe = nullptr;   // element of each point (global index)
     void* pw = nullptr;      // 1D Lagrange weights [npts][dim][np]
     void* hist = nullptr;    // [cap][npts][5] deviations from the free stream
-    int* count = nullptr;    // device record counter
-    int* overflow = nullptr;
+    int* count = nullptr;    // device int[3]: records, steps seen, overflow flag
 };
 
 }  // namespace
@@ -197,10 +196,10 @@ int L_sample(fr_ctx* c, Surface& sf, cudaStream_t s) {
     c->launches += 2;
     return c->dim == 2 ? frl::sample<Real, 2>(c->p, static_cast<const Real*>(c->u0), sf.pe,
                                               static_cast<const Real*>(sf.pw), sf.npts, ph,
-                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.overflow, s)
+                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.every, s)
                        : frl::sample<Real, 3>(c->p, static_cast<const Real*>(c->u0), sf.pe,
                                               static_cast<const Real*>(sf.pw), sf.npts, ph,
-                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.overflow, s);
+                                              static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.every, s);
 }
 
 // Optional per-launch event pairs for fr_profile_step: kind 0..3.
@@ -361,7 +360,7 @@ void release(fr_ctx* c) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
-        void* sb[] = {s.pe, s.pw, s.hist, s.count, s.overflow};
+        void* sb[] = {s.pe, s.pw, s.hist, s.count};
         for (void* b : sb)
             if (b) cudaFree(b);
     }
@@ -908,8 +907,9 @@ extern "C" int fr_integrals(fr_ctx* c, int cand, double* out) {
 }
 
 // ---------------------------------------------------------------- FW-H surfaces
-extern "C" int fwh_register(fr_ctx* c, int cand, int npts, const double* xyz, int capacity, int* handle) {
-    if (!c || !xyz || !handle || npts < 1 || capacity < 1 || cand < 0 || cand >= c->ncand)
+extern "C" int fwh_register(fr_ctx* c, int cand, int npts, const double* xyz, int capacity, int every,
+                            int* handle) {
+    if (!c || !xyz || !handle || npts < 1 || capacity < 1 || every < 1 || cand < 0 || cand >= c->ncand)
         return fail(FR_EINVAL, "bad argument");
     const int dim = c->dim;
     const int q = c->q[cand];
@@ -1016,18 +1016,17 @@ extern "C" int fwh_register(fr_ctx* c, int cand, int npts, const double* xyz, in
     sf.cand = cand;
     sf.npts = npts;
     sf.cap = capacity;
+    sf.every = every;
     int rc;
     if ((rc = upload(reinterpret_cast<void**>(&sf.pe), pe)) || (rc = upload_real(&sf.pw, pw, c->prec))) return rc;
     if (cudaMalloc(&sf.hist, size_t(capacity) * npts * 5 * c->rsz) != cudaSuccess ||
-        cudaMalloc(&sf.count, sizeof(int)) != cudaSuccess || cudaMalloc(&sf.overflow, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&sf.count, 3 * sizeof(int)) != cudaSuccess) {
         if (sf.hist) cudaFree(sf.hist);
-        if (sf.count) cudaFree(sf.count);
         cudaFree(sf.pe);
         cudaFree(sf.pw);
         return fail(FR_ENOMEM, "cannot allocate the FW-H history");
     }
-    CK(cudaMemset(sf.count, 0, sizeof(int)));
-    CK(cudaMemset(sf.overflow, 0, sizeof(int)));
+    CK(cudaMemset(sf.count, 0, 3 * sizeof(int)));
     c->surf.push_back(sf);
     invalidate_graph(c);
     *handle = int(c->surf.size()) - 1;
@@ -1037,13 +1036,21 @@ extern "C" int fwh_register(fr_ctx* c, int cand, int npts, const double* xyz, in
 extern "C" int fwh_sample(fr_ctx* c, int handle, void* stream) {
     if (!c || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad surface handle");
     Surface& sf = c->surf[handle];
-    int cnt = 0;
+    int cnt[3] = {0, 0, 0};
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    CK(cudaMemcpy(&cnt, sf.count, sizeof(int), cudaMemcpyDeviceToHost));
-    if (cnt >= sf.cap) return fail(FR_EINVAL, "FW-H history is full");
+    CK(cudaMemcpy(cnt, sf.count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (cnt[0] >= sf.cap) return fail(FR_EINVAL, "FW-H history is full");
+    // an explicit sample is taken now: align the step phase, then restore it
+    const int phase = cnt[1];
+    int aligned[3] = {cnt[0], 0, cnt[2]};
+    CK(cudaMemcpy(sf.count, aligned, sizeof(aligned), cudaMemcpyHostToDevice));
     const int rc = c->prec == FR_FP64 ? L_sample<double>(c, sf, static_cast<cudaStream_t>(stream))
                                       : L_sample<float>(c, sf, static_cast<cudaStream_t>(stream));
     CKL(rc, "sampling kernel");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    CK(cudaMemcpy(&aligned, sf.count, sizeof(aligned), cudaMemcpyDeviceToHost));
+    aligned[1] = phase;
+    CK(cudaMemcpy(sf.count, aligned, sizeof(aligned), cudaMemcpyHostToDevice));
     return FR_OK;
 }
 
@@ -1051,9 +1058,9 @@ extern "C" int fwh_history(fr_ctx* c, int handle, double* out, int* nrec) {
     if (!c || !nrec || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad argument");
     Surface& sf = c->surf[handle];
     CK(cudaDeviceSynchronize());
-    int cnt = 0, over = 0;
-    CK(cudaMemcpy(&cnt, sf.count, sizeof(int), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&over, sf.overflow, sizeof(int), cudaMemcpyDeviceToHost));
+    int ctr[3] = {0, 0, 0};
+    CK(cudaMemcpy(ctr, sf.count, sizeof(ctr), cudaMemcpyDeviceToHost));
+    const int cnt = ctr[0], over = ctr[2];
     *nrec = cnt;
     if (!out) return over ? fail(FR_EINVAL, "FW-H history overflowed") : FR_OK;
     const size_t n = size_t(cnt) * sf.npts * 5;
@@ -1077,8 +1084,7 @@ extern "C" int fwh_history(fr_ctx* c, int handle, double* out, int* nrec) {
 extern "C" int fwh_clear(fr_ctx* c, int handle) {
     if (!c || handle < 0 || handle >= int(c->surf.size())) return fail(FR_EINVAL, "bad surface handle");
     CK(cudaDeviceSynchronize());
-    CK(cudaMemset(c->surf[handle].count, 0, sizeof(int)));
-    CK(cudaMemset(c->surf[handle].overflow, 0, sizeof(int)));
+    CK(cudaMemset(c->surf[handle].count, 0, 3 * sizeof(int)));
     return FR_OK;
 }
 

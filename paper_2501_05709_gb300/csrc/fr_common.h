@@ -104,9 +104,10 @@ int forces(int P, const Real* uf, const Real* fvn, const int32_t* wall_ef, const
            int ncand, const frk::Ops<Real>& op, const frk::Geo<Real>& g, Real gm1, int viscous,
            double* fnow, double* fsum, double* fcnt, void* stream);
 
+// count: device int[3] = records, steps seen, overflow flag
 template <typename Real, int DIM>
 int sample(int P, const Real* u, const int64_t* pe, const Real* pw, int npts, const frk::Phys<Real>& ph,
-           Real* hist, int* count, int cap, int* overflow, void* stream);
+           Real* hist, int* count, int cap, int every, void* stream);
 
 template <typename Real, int DIM>
 int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,

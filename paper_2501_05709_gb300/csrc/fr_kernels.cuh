@@ -951,16 +951,19 @@ __global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ f
 // evaluates the element's tensor Lagrange interpolant (1D weights pw
 // [npts][DIM][NP] precomputed at the located reference coordinates) and
 // stores (rho, V_1, V_2, V_3, p) minus the free stream into record *count.
+// counter[0] = records written, counter[1] = steps seen, counter[2] = overflow;
+// the kernel samples only on steps that are multiples of `every`.
 template <int DIM, int P, typename Real>
 __global__ void k_sample(const Real* __restrict__ u, const int64_t* __restrict__ pe,
                          const Real* __restrict__ pw, int npts, Phys<Real> ph, Real* __restrict__ hist,
-                         const int* __restrict__ count, int cap) {
+                         const int* __restrict__ count, int cap, int every) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NV = Z::NV;
     const int lane = threadIdx.x & 31;
     const int k = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
     if (k >= npts) return;
-    const int rec = *count;
+    if (count[1] % every != 0) return;
+    const int rec = count[0];
     if (rec >= cap) return;
     const Real* ue = u + pe[k] * NV * NSP;
     const Real* wk = pw + int64_t(k) * DIM * NP;
@@ -989,11 +992,14 @@ __global__ void k_sample(const Real* __restrict__ u, const int64_t* __restrict__
     }
 }
 
-// advances a record counter after the sampling kernel of the same step
-static __global__ void k_bump(int* count, int cap, int* overflow) {
+// advances the counters after the sampling kernel of the same step
+static __global__ void k_bump(int* count, int cap, int every) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (*count < cap) *count += 1;
-        else *overflow = 1;
+        if (count[1] % every == 0) {
+            if (count[0] < cap) count[0] += 1;
+            else count[2] = 1;
+        }
+        count[1] += 1;
     }
 }
 

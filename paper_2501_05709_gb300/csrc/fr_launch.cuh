@@ -134,13 +134,13 @@ int forces<FR_REAL, FR_DIM>(int P, const FR_REAL* uf, const FR_REAL* fvn, const 
 
 template <>
 int sample<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const int64_t* pe, const FR_REAL* pw, int npts,
-                            const frk::Phys<FR_REAL>& ph, FR_REAL* hist, int* count, int cap, int* overflow,
+                            const frk::Phys<FR_REAL>& ph, FR_REAL* hist, int* count, int cap, int every,
                             void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const unsigned blocks = unsigned((int64_t(npts) * 32 + 255) / 256);
 #define C(PP) ((npts > 0 ? (frk::k_sample<FR_DIM, PP, FR_REAL><<<blocks, 256, 0, s>>>(u, pe, pw, npts, ph, hist, \
-                                                                                  count, cap), 0) : 0),        \
-               frk::k_bump<<<1, 32, 0, s>>>(count, cap, overflow), int(cudaGetLastError()))
+                                                                                  count, cap, every), 0) : 0), \
+               frk::k_bump<<<1, 32, 0, s>>>(count, cap, every), int(cudaGetLastError()))
     FR_DISPATCH(C)
 #undef C
 }

@@ -71,7 +71,7 @@ _SIGS = {
     "fr_forces": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_forces_reset": (C.c_int, [C.c_void_p]),
     "fr_integrals": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
-    "fwh_register": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "fwh_register": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "fwh_sample": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fwh_history": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
     "fwh_clear": (C.c_int, [C.c_void_p, C.c_int]),
@@ -264,10 +264,10 @@ def fr_integrals(ctx, cand=-1):
     return out
 
 
-def fwh_register(ctx, cand, xyz, capacity):
+def fwh_register(ctx, cand, xyz, capacity, every=1):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     h = C.c_int()
-    _check(lib().fwh_register(ctx.handle, cand, xyz.shape[0], _ptr(xyz), int(capacity), C.byref(h)))
+    _check(lib().fwh_register(ctx.handle, cand, xyz.shape[0], _ptr(xyz), int(capacity), int(every), C.byref(h)))
     return h.value
 
 

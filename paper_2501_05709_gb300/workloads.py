@@ -27,8 +27,9 @@ Workload recipes (paper Section 3.1 and Appendix C shapes):
   displacement and/or with walls on the y faces.
 * ``ogrid_mesh``: spanwise-periodic O-grid of quadratic hexahedra around a
   NACA 4-digit section (Section 3.4 parametrisation; surface nodes uniform in
-  arc length) or a circle, straight radial rays to a circular far field
-  centred at (0.5, 0), geometric radial stretching.
+  arc length) or a circle; straight grid lines along the (smoothed) body
+  normal to a circular far field centred at (0.5, 0); geometric radial
+  stretching.
 * ``isentropic_vortex``, ``taylor_green``: closed-form flow fields.
 * ``perturbed_uniform``: free stream plus a seeded uniform velocity
   perturbation per solution point (PCG64).
@@ -228,6 +229,25 @@ def ogrid_mesh(n_theta, n_r, n_z, span, r_outer=10.0, first_cell=2e-3, body="nac
     jr = np.arange(q * n_r + 1) / q
     s = (ratio ** jr - 1.0) / (ratio ** n_r - 1.0)
     zz = span * np.arange(q * n_z) / (q * n_z)
+    # straight grid lines along the body normal, smoothed along the surface
+    # (the trailing-edge corner fans out over several nodes), each ending
+    # where it meets the far-field circle; near the wall the cells are then
+    # wall-normal, and lines of a convex body never cross
+    tx = np.roll(xs, -1) - np.roll(xs, 1)
+    ty = np.roll(ys, -1) - np.roll(ys, 1)
+    ang = np.unwrap(np.arctan2(tx, -ty))        # outward normal (-ty, tx) of the clockwise traversal
+    wdt = max(2, nt // 6)
+    ker = np.exp(-0.5 * (np.arange(-3 * wdt, 3 * wdt + 1) / wdt) ** 2)
+    ker /= ker.sum()
+    turn = ang[-1] - ang[0] + (ang[1] - ang[0])  # one full turn (+-2 pi) over the closed curve
+    ext = np.concatenate([ang[-3 * wdt:] - turn, ang, ang[:3 * wdt] + turn])
+    angs = np.convolve(ext, ker, mode="valid")
+    vx, vy = np.cos(angs), np.sin(angs)
+    ddx, ddy = xs - cx, ys - cy
+    dv = ddx * vx + ddy * vy
+    tt = -dv + np.sqrt(dv * dv - (ddx * ddx + ddy * ddy) + r_outer ** 2)
+    xo = xs + tt * vx
+    yo = ys + tt * vy
     grid = np.empty((nt, q * n_r + 1, q * n_z, 3))
     for k, z in enumerate(zz):
         grid[:, :, k, 0] = (1 - s[None, :]) * xs[:, None] + s[None, :] * xo[:, None]

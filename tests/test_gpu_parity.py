@@ -220,3 +220,24 @@ def test_residual_accepts_unaligned_buffers(precision):
         F.fr_residual(ctx, torch.tensor(u, dtype=dt, device="cuda"), ref)
         torch.cuda.synchronize()
     assert torch.equal(Rbig[3:].view(u.shape), ref)
+
+
+def test_sampling_interval():
+    # every=3 over 7 steps: records at steps 0, 3, 6 equal to every-step sampling
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    c = make_case("ns3d_ogrid_p3")
+    m, _ = oracle_for(c)
+    u = c["state"](m.xsp)
+    y, _, _ = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.1, span=0.2)
+    with _load(c, 1) as a, _load(c, 1) as b:
+        F.fr_state_set(a, u)
+        F.fr_state_set(b, u)
+        ha = F.fwh_register(a, 0, y, 3, 3)
+        hb = F.fwh_register(b, 0, y, 7, 1)
+        F.fr_rk_step_graph(a, 7)
+        F.fr_rk_step(b, 7)
+        ra = F.fwh_history(a, ha, len(y))
+        rb = F.fwh_history(b, hb, len(y))
+    assert ra.shape[0] == 3 and rb.shape[0] == 7
+    assert np.array_equal(ra, rb[[0, 3, 6]])
