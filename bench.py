@@ -192,7 +192,7 @@ def build_workload(name):
     rho, vel, pinf = free
 
     def opts(prec):
-        return C.naca_setup(n_theta=2, n_r=1, n_z=1, precision=prec, dt=3e-6)[2]
+        return C.naca_options(precision=prec, dt=3e-6)[0]
 
     def state(ctx):
         return np.concatenate([W.perturbed_uniform(len(n), ctx.nsp, rho, vel, pinf, amplitude=0.01, seed=k)

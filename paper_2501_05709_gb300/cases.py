@@ -19,18 +19,24 @@ from . import workloads as W
 GAMMA = 1.4
 
 
-def naca_setup(naca=(0.02, 0.4, 0.12), n_theta=250, n_r=100, n_z=4, span=0.2, r_outer=10.0, first_cell=2e-3,
-               mach=0.2, aoa_deg=3.0, reynolds=23000.0, order=3, precision=F.FR_FP32, dt=3e-6):
-    """Mesh (quadratic O-grid), options and free stream of one candidate."""
-    nodes, conn = W.ogrid_mesh(n_theta, n_r, n_z, span, r_outer=r_outer, first_cell=first_cell, body="naca",
-                               naca=naca)
+def naca_options(span=0.2, mach=0.2, aoa_deg=3.0, reynolds=23000.0, order=3, precision=F.FR_FP32, dt=3e-6):
+    """Options and free stream (rho=1, |V|=1 at the angle of attack, chord 1)."""
     rho, vel, p = W.freestream(mach, aoa_deg)
     a = math.radians(aoa_deg)
     opts = F.options(order=order, precision=precision, viscous=True, mu=rho * 1.0 * 1.0 / reynolds,
                      rho_inf=rho, p_inf=p, vel_inf=tuple(vel), dt=dt,
                      lift_dir=(-math.sin(a), math.cos(a), 0.0), drag_dir=(math.cos(a), math.sin(a), 0.0),
                      ref_area=1.0 * span)
-    return nodes, conn, opts, (rho, vel, p)
+    return opts, (rho, vel, p)
+
+
+def naca_setup(naca=(0.02, 0.4, 0.12), n_theta=250, n_r=100, n_z=4, span=0.2, r_outer=10.0, first_cell=2e-3,
+               mach=0.2, aoa_deg=3.0, reynolds=23000.0, order=3, precision=F.FR_FP32, dt=3e-6):
+    """Mesh (quadratic O-grid), options and free stream of one candidate."""
+    nodes, conn = W.ogrid_mesh(n_theta, n_r, n_z, span, r_outer=r_outer, first_cell=first_cell, body="naca",
+                               naca=naca)
+    opts, free = naca_options(span, mach, aoa_deg, reynolds, order, precision, dt)
+    return nodes, conn, opts, free
 
 
 def oaspl_from_history(hist, surface, dtau, observer, free, mach_vec, span, ncopies, stream=None):
