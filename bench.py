@@ -155,10 +155,12 @@ WORKLOADS = {
                 "Rusanov+BR2, RK4 dt=1.5e-4",
     "naca100k_p3": "NACA 2412 (m=0.02, p=0.4, t=0.12) spanwise-periodic O-grid, 250x100x4 = 100,000 quadratic "
                    "hexes, span 0.2c, FR p=3 (6,400,000 DOF), Re=23000, M=0.2, AoA 3 deg, 1% seeded noise, "
-                   "RK4 dt=3e-6, wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled every step",
+                   "RK4 dt=2.53e-6 (CFL estimate), wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled "
+                   "every step",
     "batch12_p3": "12 NACA 4-digit candidates (PCG64 seed 1: m~U[0,0.06], p~U[0.2,0.6], t~U[0.08,0.16], "
                   "20k-80k quadratic hexes each, 599,888 in total, 38.4M DOF) in one context, FR p=3, Re=23000, "
-                  "M=0.2, AoA 3 deg, RK4 dt=3e-6, forces and one FW-H cylinder per candidate every step",
+                  "M=0.2, AoA 3 deg, RK4 at each candidate's own stable dt (0.8e-6..3.4e-6), forces and one FW-H "
+                  "cylinder per candidate every step",
 }
 
 
@@ -178,17 +180,18 @@ def build_workload(name):
 
         def state(ctx):
             return np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=MACH), 0, 1))
-        return [(nodes, conn)], opts, state, [], False
+        return [(nodes, conn)], opts, state, [], False, None
     if name == "naca100k_p3":
         params = [{"naca": (0.02, 0.4, 0.12), "n_theta": 250, "n_r": 100}]
     elif name == "batch12_p3":
         params = C.batch_params(12, seed=1)
     else:
         raise SystemExit(f"unknown workload {name}")
-    meshes, free, o32 = [], None, None
+    meshes, free, dts = [], None, []
     for prm in params:
         nodes, conn, _, free = C.naca_setup(naca=prm["naca"], n_theta=prm["n_theta"], n_r=prm["n_r"])
         meshes.append((nodes, conn))
+        dts.append(C.stable_dt(nodes, prm["n_theta"]))
     rho, vel, pinf = free
 
     def opts(prec):
@@ -198,7 +201,7 @@ def build_workload(name):
         return np.concatenate([W.perturbed_uniform(len(n), ctx.nsp, rho, vel, pinf, amplitude=0.01, seed=k)
                                for k, (n, _) in enumerate(meshes)])
     surf = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=0.2)[0]
-    return meshes, opts, state, [surf] * len(meshes), True
+    return meshes, opts, state, [surf] * len(meshes), True, dts
 
 
 def gpu_leg(args, rank, world, local_rank):
@@ -211,12 +214,14 @@ def gpu_leg(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     B.build()
-    meshes, opts, state_of, surfaces, curved = build_workload(args.workload)
+    meshes, opts, state_of, surfaces, curved, dts = build_workload(args.workload)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     prec = F.FR_FP32 if args.precision == "fp32" else F.FR_FP64
     rsz = 4 if prec == F.FR_FP32 else 8
     ctx = F.fr_mesh_load(meshes, opts(prec))
+    for k, d in enumerate(dts or []):
+        F.fr_set_cand_dt(ctx, k, d)
     p = ctx.order
     u0 = state_of(ctx)
     E, nsp = ctx.nelem, ctx.nsp
@@ -300,6 +305,8 @@ def gpu_leg(args, rank, world, local_rank):
     fp64 = None
     if not args.no_fp64 and prec == F.FR_FP32:
         c64 = F.fr_mesh_load(meshes, opts(F.FR_FP64))
+        for k, d in enumerate(dts or []):
+            F.fr_set_cand_dt(c64, k, d)
         F.fr_state_set(c64, u0)
         for k, srf in enumerate(surfaces):
             F.fwh_register(c64, k, srf, cap, 1)

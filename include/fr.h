@@ -144,6 +144,12 @@ int fr_residual(fr_ctx* ctx, const void* u, void* R, void* stream);
  * synchronising. */
 int fr_rk_step(fr_ctx* ctx, int nsteps, void* stream);
 
+/* Per-candidate time step (the batched MADS poll of Section 2.2 advances
+ * candidates of uneven meshes together, each at its own stable step): every
+ * element of candidate cand uses dt from now on (fr_options.dt until set).
+ * Errors: FR_EINVAL (cand out of range, dt <= 0), FR_ENOMEM. */
+int fr_set_cand_dt(fr_ctx* ctx, int cand, double dt);
+
 /* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
  * use for the current surfaces and options).  Bit-identical results. */
 int fr_rk_step_graph(fr_ctx* ctx, int nsteps, void* stream);

@@ -39,6 +39,24 @@ def naca_setup(naca=(0.02, 0.4, 0.12), n_theta=250, n_r=100, n_z=4, span=0.2, r_
     return nodes, conn, opts, free
 
 
+def first_cell_thickness(nodes, n_theta):
+    """Smallest wall-normal thickness of the first element ring of an O-grid
+    (elements 0..n_theta-1 of the first spanwise layer, nodes at xi_2 = -1, +1)."""
+    X = np.asarray(nodes)[:n_theta].reshape(n_theta, 3, 3, 3, 3)
+    wall = X[:, 0, 0, :, :2]
+    off = X[:, 0, 2, :, :2]
+    t = wall[:, 2] - wall[:, 0]
+    t /= np.linalg.norm(t, axis=1)[:, None]
+    nrm = np.stack([-t[:, 1], t[:, 0]], axis=1)
+    return float(np.abs(np.einsum("ij,ij->i", off[:, 1] - wall[:, 1], nrm)).min())
+
+
+def stable_dt(nodes, n_theta, mach=0.2, order=3, cfl=1.0):
+    """Explicit RK4 step estimate cfl * h_min / ((p+1)^2 (|V| + c)) with |V| = 1,
+    c = 1/M and h_min the first-ring wall-normal thickness."""
+    return cfl * first_cell_thickness(nodes, n_theta) / ((order + 1) ** 2 * (1.0 + 1.0 / mach))
+
+
 def oaspl_from_history(hist, surface, dtau, observer, free, mach_vec, span, ncopies, stream=None):
     """FW-H (libfr fwh_integrate) of a history [nrec, npts, 5] -> (t*, p', p'_rms,
     OASPL in dB re 20 uPa with p_inf scaled to 101325 Pa), or raises FrError
@@ -61,6 +79,12 @@ def run_naca(steps=2000, precision=F.FR_FP32, sample_every=1, ncopies=1, observe
     """One candidate: perturbed free stream (1% seeded velocity noise), `steps`
     RK4 steps, forces every step, the FW-H surface sampled every
     `sample_every` steps, then FW-H at the observer.  Returns a dict."""
+    if mesh_kw.get("dt") is None:
+        mesh_kw.pop("dt", None)
+        probe = W.ogrid_mesh(mesh_kw.get("n_theta", 250), 1, 1, mesh_kw.get("span", 0.2),
+                             r_outer=mesh_kw.get("r_outer", 10.0), first_cell=mesh_kw.get("first_cell", 2e-3),
+                             naca=mesh_kw.get("naca", (0.02, 0.4, 0.12)))[0]
+        mesh_kw["dt"] = stable_dt(probe, mesh_kw.get("n_theta", 250))
     nodes, conn, opts, free = naca_setup(precision=precision, **mesh_kw)
     span = mesh_kw.get("span", 0.2)
     rho, vel, p = free
@@ -113,22 +137,26 @@ def batch_params(n=12, seed=1):
     return out
 
 
-def run_batch(params, steps, precision=F.FR_FP32, dt=3e-6, sample_every=1, surface_radius=1.5, seed=0,
+def run_batch(params, steps, precision=F.FR_FP32, dt=None, sample_every=1, surface_radius=1.5, seed=0,
               graph=True):
     """All candidates in one context (concatenated elements; one graph-replayed
-    launch sequence per RK4 step).  Returns per-candidate mean C_L, C_D, the
-    histories and the throughput."""
+    launch sequence per RK4 step), each at its own stable time step unless dt
+    is given.  Returns per-candidate mean C_L, C_D, the histories and the
+    throughput."""
     import torch
-    meshes, frees, opts = [], None, None
+    meshes, frees, opts, dts = [], None, None, []
     for k, prm in enumerate(params):
         nodes, conn, o, free = naca_setup(naca=prm["naca"], n_theta=prm["n_theta"], n_r=prm["n_r"],
                                          precision=precision, dt=dt)
         meshes.append((nodes, conn))
         frees, opts = free, o
+        dts.append(stable_dt(nodes, prm["n_theta"]) if dt is None else dt)
     rho, vel, p = frees
     surface = W.cylinder_surface(radius=surface_radius, center=(0.5, 0.0), spacing=0.01, span=0.2)
-    res = {"candidates": len(params), "elements": [len(n) for n, _ in meshes], "steps": steps}
+    res = {"candidates": len(params), "elements": [len(n) for n, _ in meshes], "steps": steps, "dt": dts}
     with F.fr_mesh_load(meshes, opts) as ctx:
+        for k, d in enumerate(dts):
+            F.fr_set_cand_dt(ctx, k, d)
         us = [W.perturbed_uniform(len(n), ctx.nsp, rho, vel, p, amplitude=0.01, seed=seed + k)
               for k, (n, _) in enumerate(meshes)]
         F.fr_state_set(ctx, np.concatenate(us))

@@ -78,6 +78,7 @@ struct fr_ctx {
     int64_t graph_launches_per_step = 0;
     int device = 0;
     double* stage64 = nullptr;  // double staging buffer for FP32 state transfers
+    void* dte = nullptr;        // per-element time step (Real[E]) once a candidate sets its own
 };
 
 namespace {
@@ -266,6 +267,7 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         frk::Stage<Real> st;
         st.stage = stage;
         st.dt = Real(c->opt.dt);
+        st.dte = static_cast<const Real*>(c->dte);
         st.R = nullptr;
         st.u0 = u0;
         st.us = us;
@@ -294,6 +296,7 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     frk::Stage<Real> st;
     st.stage = 0;
     st.dt = Real(0);
+    st.dte = nullptr;
     st.R = R;
     st.u0 = st.us = st.acc = st.uf_next = nullptr;
     rc = L_resid<Real>(c, u, uf, st, s);
@@ -356,7 +359,7 @@ size_t smem_of(const fr_ctx* c, int kernel, int epb) {
 void release(fr_ctx* c) {
     if (!c) return;
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
-                    c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64};
+                    c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -652,12 +655,12 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         c->E = 0;
         int r0, r1, r2;
         if (c->prec == FR_FP64) {
-            frk::Stage<double> st{0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr};
+            frk::Stage<double> st{0, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
             r0 = L_traces<double>(c, nullptr, nullptr, nullptr);
             r1 = L_visc<double>(c, nullptr, nullptr, nullptr);
             r2 = L_resid<double>(c, nullptr, nullptr, st, nullptr);
         } else {
-            frk::Stage<float> st{0, 0.0f, nullptr, nullptr, nullptr, nullptr, nullptr};
+            frk::Stage<float> st{0, 0.0f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
             r0 = L_traces<float>(c, nullptr, nullptr, nullptr);
             r1 = L_visc<float>(c, nullptr, nullptr, nullptr);
             r2 = L_resid<float>(c, nullptr, nullptr, st, nullptr);
@@ -834,6 +837,38 @@ extern "C" int fr_rk_step_graph(fr_ctx* c, int nsteps, void* stream) {
         CK(cudaGraphLaunch(c->gexec, s));
         c->launches += c->graph_launches_per_step;
     }
+    return FR_OK;
+}
+
+__global__ void k_fill_d(double* a, int64_t n, double v) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        a[i] = v;
+}
+__global__ void k_fill_f(float* a, int64_t n, float v) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        a[i] = v;
+}
+
+extern "C" int fr_set_cand_dt(fr_ctx* c, int cand, double dt) {
+    if (!c || cand < 0 || cand >= c->ncand || !(dt > 0.0)) return fail(FR_EINVAL, "bad candidate or dt");
+    CK(cudaDeviceSynchronize());
+    if (!c->dte) {
+        if (cudaMalloc(&c->dte, size_t(c->E) * c->rsz) != cudaSuccess) {
+            c->dte = nullptr;
+            return fail(FR_ENOMEM, "cannot allocate per-element time steps");
+        }
+        if (c->prec == FR_FP64) k_fill_d<<<256, 256>>>(static_cast<double*>(c->dte), c->E, c->opt.dt);
+        else k_fill_f<<<256, 256>>>(static_cast<float*>(c->dte), c->E, float(c->opt.dt));
+        c->launches += 1;
+        CK(cudaGetLastError());
+        invalidate_graph(c);  // the captured step read the scalar dt
+    }
+    const int64_t a0 = c->cand_off[cand], n = c->cand_off[cand + 1] - a0;
+    if (c->prec == FR_FP64) k_fill_d<<<256, 256>>>(static_cast<double*>(c->dte) + a0, n, dt);
+    else k_fill_f<<<256, 256>>>(static_cast<float*>(c->dte) + a0, n, float(dt));
+    c->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
     return FR_OK;
 }
 
@@ -1136,7 +1171,8 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
                     if (kern == 0) rc = L_traces<double>(c, u, uf, nullptr);
                     else if (kern == 1) rc = L_visc<double>(c, u, uf, nullptr);
                     else {
-                        frk::Stage<double> st{0, 0.0, static_cast<double*>(R), nullptr, nullptr, nullptr, nullptr};
+                        frk::Stage<double> st{0, 0.0, nullptr, static_cast<double*>(R), nullptr, nullptr, nullptr,
+                                              nullptr};
                         rc = L_resid<double>(c, u, uf, st, nullptr);
                     }
                 } else {
@@ -1145,7 +1181,8 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
                     if (kern == 0) rc = L_traces<float>(c, u, uf, nullptr);
                     else if (kern == 1) rc = L_visc<float>(c, u, uf, nullptr);
                     else {
-                        frk::Stage<float> st{0, 0.0f, static_cast<float*>(R), nullptr, nullptr, nullptr, nullptr};
+                        frk::Stage<float> st{0, 0.0f, nullptr, static_cast<float*>(R), nullptr, nullptr, nullptr,
+                                             nullptr};
                         rc = L_resid<float>(c, u, uf, st, nullptr);
                     }
                 }

@@ -60,10 +60,12 @@ struct Geo {
 //   stage 3: input us;  acc += dt/3 k3;       us = u0 + dt k3
 //   stage 4: input us;  u0 = u0 + acc + dt/6 k4
 // uf_next (stages 1-4): traces of the stage's output state, for the next stage.
+// dte (optional): per-element time step overriding dt.
 template <typename Real>
 struct Stage {
     int stage;
     Real dt;
+    const Real* dte;
     Real* R;          // stage 0 output
     Real* u0;
     Real* us;

@@ -822,6 +822,7 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
     }
     // F: residual and RK stage per solution point; the new stage state
     // replaces su for the traces
+    const Real dt = st.dte ? st.dte[e] : st.dt;
 #pragma unroll
     for (int s = 0; s < NSPW; ++s) {
         const int sp = lane + 32 * s;
@@ -849,22 +850,22 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                     nu = su[k];
                     break;
                 case 1:
-                    st.acc[gi] = (st.dt * Real(1.0 / 6.0)) * r;
-                    nu = su[k] + (st.dt * Real(0.5)) * r;
+                    st.acc[gi] = (dt * Real(1.0 / 6.0)) * r;
+                    nu = su[k] + (dt * Real(0.5)) * r;
                     st.us[gi] = nu;
                     break;
                 case 2:
-                    st.acc[gi] = accv + (st.dt * Real(1.0 / 3.0)) * r;
-                    nu = u0v + (st.dt * Real(0.5)) * r;
+                    st.acc[gi] = accv + (dt * Real(1.0 / 3.0)) * r;
+                    nu = u0v + (dt * Real(0.5)) * r;
                     st.us[gi] = nu;
                     break;
                 case 3:
-                    st.acc[gi] = accv + (st.dt * Real(1.0 / 3.0)) * r;
-                    nu = u0v + st.dt * r;
+                    st.acc[gi] = accv + (dt * Real(1.0 / 3.0)) * r;
+                    nu = u0v + dt * r;
                     st.us[gi] = nu;
                     break;
                 default:
-                    nu = u0v + accv + (st.dt * Real(1.0 / 6.0)) * r;
+                    nu = u0v + accv + (dt * Real(1.0 / 6.0)) * r;
                     st.u0[gi] = nu;
                     break;
             }

@@ -68,6 +68,7 @@ _SIGS = {
     "fr_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_rk_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_rk_step_graph": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fr_set_cand_dt": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "fr_forces": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_forces_reset": (C.c_int, [C.c_void_p]),
     "fr_integrals": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -242,6 +243,10 @@ def fr_residual(ctx, u, R, stream=None):
 
 def fr_rk_step(ctx, nsteps, stream=None):
     _check(lib().fr_rk_step(ctx.handle, int(nsteps), _stream(stream)))
+
+
+def fr_set_cand_dt(ctx, cand, dt):
+    _check(lib().fr_set_cand_dt(ctx.handle, int(cand), float(dt)))
 
 
 def fr_rk_step_graph(ctx, nsteps, stream=None):

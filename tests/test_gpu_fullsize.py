@@ -176,7 +176,10 @@ def test_batched_candidates_match_separate_runs():
                      ref_area=0.2)
     states = [W.perturbed_uniform(len(n), 64, rho, vel, p, amplitude=0.01, seed=k) for k, (n, c) in enumerate(meshes)]
     y, _, _ = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.1, span=0.2)
+    dts = [2e-5, 3e-5, 1.5e-5]
     with F.fr_mesh_load(meshes, opts) as batch:
+        for k, d in enumerate(dts):
+            F.fr_set_cand_dt(batch, k, d)
         F.fr_state_set(batch, np.concatenate(states))
         hs = [F.fwh_register(batch, k, y, 8) for k in range(3)]
         F.fr_rk_step_graph(batch, 4)
@@ -185,6 +188,7 @@ def test_batched_candidates_match_separate_runs():
         hb = [F.fwh_history(batch, h, len(y)) for h in hs]
     off = 0
     for k, (n, c) in enumerate(meshes):
+        opts.dt = dts[k]
         with F.fr_mesh_load((n, c), opts) as one:
             F.fr_state_set(one, states[k])
             h = F.fwh_register(one, 0, y, 8)
