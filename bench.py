@@ -155,11 +155,11 @@ WORKLOADS = {
                 "Rusanov+BR2, RK4 dt=1.5e-4",
     "naca100k_p3": "NACA 2412 (m=0.02, p=0.4, t=0.12) spanwise-periodic O-grid, 250x100x4 = 100,000 quadratic "
                    "hexes, span 0.2c, FR p=3 (6,400,000 DOF), Re=23000, M=0.2, AoA 3 deg, 1% seeded noise, "
-                   "RK4 dt=2.53e-6 (CFL estimate), wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled "
+                   "RK4 dt=1.37e-6 (advective+viscous CFL estimate), wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled "
                    "every step",
     "batch12_p3": "12 NACA 4-digit candidates (PCG64 seed 1: m~U[0,0.06], p~U[0.2,0.6], t~U[0.08,0.16], "
                   "20k-80k quadratic hexes each, 599,888 in total, 38.4M DOF) in one context, FR p=3, Re=23000, "
-                  "M=0.2, AoA 3 deg, RK4 at each candidate's own stable dt (0.8e-6..3.4e-6), forces and one FW-H "
+                  "M=0.2, AoA 3 deg, RK4 at each candidate's own stable dt (0.27e-6..2.0e-6), forces and one FW-H "
                   "cylinder per candidate every step",
 }
 

@@ -51,10 +51,13 @@ def first_cell_thickness(nodes, n_theta):
     return float(np.abs(np.einsum("ij,ij->i", off[:, 1] - wall[:, 1], nrm)).min())
 
 
-def stable_dt(nodes, n_theta, mach=0.2, order=3, cfl=1.0):
-    """Explicit RK4 step estimate cfl * h_min / ((p+1)^2 (|V| + c)) with |V| = 1,
-    c = 1/M and h_min the first-ring wall-normal thickness."""
-    return cfl * first_cell_thickness(nodes, n_theta) / ((order + 1) ** 2 * (1.0 + 1.0 / mach))
+def stable_dt(nodes, n_theta, mach=0.2, order=3, reynolds=23000.0, cfl=0.8):
+    """Explicit RK4 step estimate from the advective and viscous rates of the
+    thinnest first-ring cell: dt = cfl / ((p+1)^2 (|V| + c) / h + (p+1)^4 nu / h^2)
+    with |V| = 1, c = 1/M, nu = 1/Re and h the wall-normal thickness."""
+    h = first_cell_thickness(nodes, n_theta)
+    k = (order + 1) ** 2
+    return cfl / (k * (1.0 + 1.0 / mach) / h + k * k / reynolds / (h * h))
 
 
 def oaspl_from_history(hist, surface, dtau, observer, free, mach_vec, span, ncopies, stream=None):
