@@ -237,6 +237,12 @@ int fwh_integrate_noalloc(const double* hist, int nt, int npts, const double* y,
 int fr_set_tile(fr_ctx* ctx, int elems_per_block);
 int fr_autotune(fr_ctx* ctx, int* best);
 
+/* Measurement aid (no counterpart in the paper): FP64 fused multiply-add
+ * throughput of this GPU in GFLOP/s (2 flops per FMA), from a kernel of
+ * independent FMA chains timed with CUDA events on stream.  The FP64 FR path
+ * is bound by this rate rather than by memory bandwidth. */
+int fr_probe_fp64_peak(double* gflops, void* stream);
+
 /* Counts of kernels launched by this context since creation (for
  * benchmarking claims). */
 int64_t fr_launch_count(const fr_ctx* ctx);

@@ -1210,6 +1210,46 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
 
 extern "C" int64_t fr_launch_count(const fr_ctx* c) { return c ? c->launches : 0; }
 
+// Independent FMA chains per thread; the result is stored so nothing is elided.
+__global__ void k_dfma_probe(double* out, int iters, double a, double b) {
+    double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+    double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+extern "C" int fr_probe_fp64_peak(double* gflops, void* stream) {
+    if (!gflops) return fail(FR_EINVAL, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return fail(FR_ENOMEM, "probe buffer");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);  // warm-up
+    cudaEventRecord(a, s);
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) k_dfma_probe<<<blocks, threads, 0, s>>>(out, iters, 0.999999, 1e-7);
+    cudaEventRecord(b, s);
+    const cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess) return fail(FR_ECUDA, cudaGetErrorString(e));
+    const double flops = 2.0 * 8.0 * double(iters) * blocks * threads * reps;
+    *gflops = flops / (double(ms) * 1e-3) / 1e9;
+    return FR_OK;
+}
+
 extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_out[4], int64_t n_out[4]) {
     if (!c || nsteps < 0 || !ms_out || !n_out) return fail(FR_EINVAL, "bad argument");
     Prof pr;

@@ -87,6 +87,7 @@ _SIGS = {
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
     "fr_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_probe_fp64_peak": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
 }
 
 
@@ -325,6 +326,13 @@ def fr_autotune(ctx):
 
 def fr_launch_count(ctx):
     return int(lib().fr_launch_count(ctx.handle))
+
+
+def fr_probe_fp64_peak(stream=None):
+    """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
+    g = C.c_double()
+    _check(lib().fr_probe_fp64_peak(C.byref(g), _stream(stream)))
+    return g.value
 
 
 def fr_profile_step(ctx, nsteps, stream=None):
