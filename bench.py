@@ -142,9 +142,11 @@ def algorithmic_bytes(E, p, rsz, viscous=True, dim=3, curved=False):
     traces = E * (u + tr)
     visc = E * (u + tr + tr + geo) if viscous else 0
     rk = (2 + 4 + 4 + 3) / 4.0 * u
-    # residual: u, neighbour traces, own+neighbour viscous fluxes, metrics,
-    # RK stage arrays (stage-averaged) and the traces of the updated state
-    resid = E * (u + tr + (2 * tr if viscous else 0) + geo + rk + tr)
+    # residual: u, neighbour traces, the viscous-flux array (each face's
+    # entries are read by both elements of the face, but the array need only
+    # move once), metrics, RK stage arrays (stage-averaged) and the traces of
+    # the updated state
+    resid = E * (u + tr + (tr if viscous else 0) + geo + rk + tr)
     return {"traces": traces, "visc": visc, "resid": resid}
 
 

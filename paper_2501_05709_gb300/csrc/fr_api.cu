@@ -547,25 +547,33 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
             }
     }
 
-    // ---- affine detection: constant metrics per element and normals per face
+    // ---- affine detection: constant metrics per element and normals per face.
+    // Each metric row S[d][:] (the area vector of the xi_d faces) and each
+    // face normal is compared against its own largest component, so round-off
+    // in components that vanish analytically (axis-aligned elements) does not
+    // count as variation.
     bool affine = true;
     for (int64_t e = 0; e < E && affine; ++e) {
-        for (int k = 0; k < dim * dim && affine; ++k) {
-            const double* s = &Sh[(e * dim * dim + k) * nsp];
+        for (int d = 0; d < dim && affine; ++d) {
             double mx = 0;
-            for (int sp = 0; sp < nsp; ++sp) mx = std::max(mx, std::fabs(s[sp]));
-            for (int sp = 1; sp < nsp; ++sp)
-                if (std::fabs(s[sp] - s[0]) > 1e-13 * (mx + 1e-300)) affine = false;
+            for (int i = 0; i < dim; ++i)
+                for (int sp = 0; sp < nsp; ++sp) mx = std::max(mx, std::fabs(Sh[(e * dim * dim + d * dim + i) * nsp + sp]));
+            for (int i = 0; i < dim && affine; ++i) {
+                const double* s = &Sh[(e * dim * dim + d * dim + i) * nsp];
+                for (int sp = 1; sp < nsp; ++sp)
+                    if (std::fabs(s[sp] - s[0]) > 1e-13 * mx) affine = false;
+            }
         }
         for (int sp = 1; sp < nsp && affine; ++sp)
             if (std::fabs(Jh[e * nsp + sp] - Jh[e * nsp]) > 1e-13 * std::fabs(Jh[e * nsp])) affine = false;
-        for (int f = 0; f < nf && affine; ++f)
+        for (int f = 0; f < nf && affine; ++f) {
+            const double* nv = &Nsh[(e * nf + f) * nfp * dim];
+            double mx = 0;
+            for (int k = 0; k < nfp * dim; ++k) mx = std::max(mx, std::fabs(nv[k]));
             for (int fp = 1; fp < nfp && affine; ++fp)
-                for (int i = 0; i < dim; ++i) {
-                    const double a0 = Nsh[((e * nf + f) * nfp) * dim + i];
-                    const double a1 = Nsh[((e * nf + f) * nfp + fp) * dim + i];
-                    if (std::fabs(a1 - a0) > 1e-13 * (std::fabs(a0) + 1e-300) + 1e-300) affine = false;
-                }
+                for (int i = 0; i < dim; ++i)
+                    if (std::fabs(nv[fp * dim + i] - nv[i]) > 1e-13 * mx) affine = false;
+        }
     }
     c->affine = affine ? 1 : 0;
     int rc;
@@ -577,6 +585,16 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
             for (int f = 0; f < nf; ++f)
                 for (int i = 0; i < dim; ++i) N1[(e * nf + f) * dim + i] = Nsh[((e * nf + f) * nfp) * dim + i];
         }
+        // the larger (element, face) side takes the exact negative of the
+        // smaller side's constant normal, so common fluxes stay equal and opposite
+        for (int64_t e = 0; e < E; ++e)
+            for (int f = 0; f < nf; ++f) {
+                const int32_t code = nbr[e * nf + f];
+                if (code < 0) continue;
+                const int64_t other = code >> 3;
+                if (e * nf + f > other)
+                    for (int i = 0; i < dim; ++i) N1[(e * nf + f) * dim + i] = -N1[other * dim + i];
+            }
         c->sS_e = dim * dim; c->sS_k = 1; c->sS_sp = 0;
         c->sJ_e = 1; c->sJ_sp = 0;
         c->sN_f = dim; c->sN_fp = 0;

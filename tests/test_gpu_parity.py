@@ -43,6 +43,19 @@ def test_residual_fp64(name):
     assert relerr(R, R_or) <= fp64_tol(s.residual, u)
 
 
+AFFINE = {"vortex2d_p2", "tgv3d_p3", "single_element"}
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_affine_detection(name):
+    """Straight-sided axis-aligned meshes take the per-element metric path
+    (round-off in analytically zero metric components is not variation);
+    curved meshes keep per-point metrics."""
+    c = make_case(name)
+    with _load(c) as ctx:
+        assert ctx.affine == (1 if name in AFFINE else 0)
+
+
 @pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2"])
 def test_rk4_steps_fp64(name):
     from paper_2501_05709_gb300 import fr as F
