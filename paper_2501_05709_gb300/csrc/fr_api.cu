@@ -351,9 +351,11 @@ void default_launch(fr_ctx* c) {
 }
 
 size_t smem_of(const fr_ctx* c, int kernel, int epb) {
+    const bool cv = !c->affine;
     if (c->prec == FR_FP64)
-        return c->dim == 2 ? frl::smem_bytes<double, 2>(c->p, kernel, epb) : frl::smem_bytes<double, 3>(c->p, kernel, epb);
-    return c->dim == 2 ? frl::smem_bytes<float, 2>(c->p, kernel, epb) : frl::smem_bytes<float, 3>(c->p, kernel, epb);
+        return c->dim == 2 ? frl::smem_bytes<double, 2>(c->p, kernel, epb, cv)
+                           : frl::smem_bytes<double, 3>(c->p, kernel, epb, cv);
+    return c->dim == 2 ? frl::smem_bytes<float, 2>(c->p, kernel, epb, cv) : frl::smem_bytes<float, 3>(c->p, kernel, epb, cv);
 }
 
 void release(fr_ctx* c) {

@@ -115,8 +115,9 @@ template <typename Real, int DIM>
 int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,
               const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
 
-// dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual)
+// dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual);
+// curved meshes stage per-point metrics and need more
 template <typename Real, int DIM>
-size_t smem_bytes(int P, int kernel, int epb);
+size_t smem_bytes(int P, int kernel, int epb, bool curved);
 
 }  // namespace frl

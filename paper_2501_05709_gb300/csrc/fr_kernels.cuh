@@ -287,13 +287,23 @@ struct Smem {
     static constexpr int visc = vD + imax(DIM * U, F);
     static constexpr int rB = U, rC = rB + imax(U, F), rD = rC + F, rE = rD + imax(DIM * U, 2 * F);
     static constexpr int resid = rE + F;
+    // curved meshes also stage the element's S [DIM*DIM][NSP] and 1/|J| [NSP]:
+    // in an extra region after visc's, and in resid's region E once the face
+    // phase is over
+    static constexpr int G = DIM * DIM * Z::NSP + Z::NSP;
+    static constexpr int visc_c = visc + G;
+    static constexpr int resid_c = rE + imax(F, G);
 };
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
 template <int DIM, int P, typename Real>
-__host__ __device__ constexpr size_t smem_visc(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::visc; }
+__host__ __device__ constexpr size_t smem_visc(int wpb, bool curved) {
+    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::visc_c : Smem<DIM, P>::visc);
+}
 template <int DIM, int P, typename Real>
-__host__ __device__ constexpr size_t smem_resid(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::resid; }
+__host__ __device__ constexpr size_t smem_resid(int wpb, bool curved) {
+    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::resid_c : Smem<DIM, P>::resid);
+}
 
 template <int DIM, typename Real>
 __device__ __forceinline__ void load_normal(const Geo<Real>& g, int64_t e, int f, int fp, Real* N) {
@@ -309,23 +319,6 @@ __device__ __forceinline__ void load_normal(const Geo<Real>& g, int64_t e, int f
 // xi_d = +1 face uses the mirror symmetry of the GL points: l_j(+1) =
 // l_{NP-1-j}(-1) and h_+(x_i) = h_-(x_{NP-1-i}).
 
-// copy one element's N values global -> shared; 16-byte vectors only when the
-// row length, the per-warp shared stride WS and the global address allow it
-template <int N, int WS, typename Real>
-__device__ __forceinline__ void warp_load(const Real* __restrict__ g, Real* s, int lane) {
-    constexpr bool vec_ok = (N * sizeof(Real)) % 16 == 0 && (WS * sizeof(Real)) % 16 == 0;
-    if constexpr (vec_ok) {
-        if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
-            constexpr int NV4 = int(N * sizeof(Real) / 16);
-            const float4* g4 = reinterpret_cast<const float4*>(g);
-            float4* s4 = reinterpret_cast<float4*>(s);
-            for (int k = lane; k < NV4; k += 32) s4[k] = g4[k];
-            return;
-        }
-    }
-    for (int k = lane; k < N; k += 32) s[k] = g[k];
-}
-
 // metric terms S[d][i] at solution point sp (affine: one set per element)
 template <int DIM, typename Real>
 __device__ __forceinline__ void load_S(const Geo<Real>& g, int64_t e, int sp, Real* S) {
@@ -333,14 +326,113 @@ __device__ __forceinline__ void load_S(const Geo<Real>& g, int64_t e, int sp, Re
     for (int k = 0; k < DIM * DIM; ++k) S[k] = g.S[e * g.sS_e + k * g.sS_k + sp * g.sS_sp];
 }
 
-// both end values of the line of sv through face point ln in direction d:
+// ---- placement of volume data in shared memory
+// Volume arrays (state, gradients, fluxes, divergence) hold variables of NSP
+// points each; point (i0, i1, i2) of variable v.  For p = 3 in 3D with
+// 4-byte reals the 4-point rows are permuted within each variable: row
+// (i1, i2) of v sits at row (i1 ^ a, i2 ^ b) with b = v & 1 and
+// a = (i2 >> 1) | (b << 1).  Line passes put consecutive variables on lanes
+// 0-15 and 16-31, so with this placement the lines of all three directions,
+// the point-wise passes (lane = point) and the per-face-point reads each touch
+// 32 distinct banks, and every row stays a 16-byte vector along xi_0.
+template <int DIM, int P, typename Real>
+struct Vol {
+    static constexpr int NP = P + 1;
+    static constexpr int NSP = Sz<DIM, P>::NSP;
+    static constexpr bool SWZ = DIM == 3 && NP == 4 && sizeof(Real) == 4;
+    static constexpr bool ROW4 = NP == 4 && sizeof(Real) == 4;  // a row is one float4
+    __device__ __forceinline__ static int at(int v, int i0, int i1, int i2) {
+        if constexpr (SWZ) {
+            const int b = v & 1;
+            return v * NSP + 16 * (i2 ^ b) + 4 * (i1 ^ ((i2 >> 1) | (b << 1))) + i0;
+        } else {
+            return v * NSP + i0 + NP * (i1 + NP * i2);
+        }
+    }
+    // point sp = i0 + NP i1 (+ NP^2 i2) of variable v
+    __device__ __forceinline__ static int pt(int v, int sp) {
+        if constexpr (DIM == 2) return v * NSP + sp;
+        else return at(v, sp % NP, (sp / NP) % NP, sp / (NP * NP));
+    }
+    // point j of the line through face point ln in direction d (see line_sp)
+    __device__ __forceinline__ static int line(int v, int d, int ln, int j) {
+        if constexpr (DIM == 2) {
+            return v * NSP + line_sp<DIM, NP>(d, ln, j);
+        } else {
+            const int a = ln % NP, b = ln / NP;
+            if (d == 0) return at(v, j, a, b);
+            if (d == 1) return at(v, a, j, b);
+            return at(v, a, b, j);
+        }
+    }
+};
+
+// the NP values of line ln (direction d) of variable v; a direction-0 line is
+// one contiguous row (a single 16-byte access when a row is a float4)
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ void vload_line(const Real* X, int v, int d, int ln, Real (&s)[P + 1]) {
+    using V = Vol<DIM, P, Real>;
+    if constexpr (V::ROW4) {
+        if (d == 0) {
+            const float4 r = *reinterpret_cast<const float4*>(X + V::line(v, 0, ln, 0));
+            s[0] = r.x;
+            s[1] = r.y;
+            s[2] = r.z;
+            s[3] = r.w;
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < P + 1; ++j) s[j] = X[V::line(v, d, ln, j)];
+}
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ void vstore_line(Real* X, int v, int d, int ln, const Real (&s)[P + 1]) {
+    using V = Vol<DIM, P, Real>;
+    if constexpr (V::ROW4) {
+        if (d == 0) {
+            *reinterpret_cast<float4*>(X + V::line(v, 0, ln, 0)) = make_float4(s[0], s[1], s[2], s[3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < P + 1; ++j) X[V::line(v, d, ln, j)] = s[j];
+}
+
+// The (variable, line) task of a lane at iteration it of a line pass, task
+// index t = v NFP + ln.  When NFP divides 32 a lane keeps its line, and the
+// parity of its variable, at every iteration: its accesses then use the
+// reference variable vref, whose shared offsets depend on the lane only (the
+// compiler keeps them out of the loop), in an array shifted by whole
+// variables (an even number of them, so the permuted placement is unchanged).
+template <int DIM, int P>
+struct LineTask {
+    int t, v, ln, vref, shift;
+    __device__ __forceinline__ LineTask(int lane, int it) {
+        constexpr int NFP = Sz<DIM, P>::NFP, NSP = Sz<DIM, P>::NSP;
+        t = lane + 32 * it;
+        if constexpr (32 % NFP == 0 && (32 / NFP) % 2 == 0) {
+            constexpr int VPI = 32 / NFP;
+            vref = lane / NFP;
+            ln = lane % NFP;
+            v = vref + VPI * it;
+            shift = VPI * it * NSP;
+        } else {
+            v = t / NFP;
+            ln = t % NFP;
+            vref = v;
+            shift = 0;
+        }
+    }
+};
+
+// both end values of line ln (direction d) of variable v of volume array X:
 // m = sum_j l_j(-1) s_j and p = sum_j l_j(+1) s_j
 template <int DIM, int P, typename Real>
-__device__ __forceinline__ void line_ends(const Real* sv, const Ops<Real>& op, int d, int ln, Real& m, Real& p) {
+__device__ __forceinline__ void line_ends(const Real* X, int v, const Ops<Real>& op, int d, int ln, Real& m,
+                                          Real& p) {
     constexpr int NP = P + 1;
     Real s[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) s[j] = sv[line_sp<DIM, NP>(d, ln, j)];
+    vload_line<DIM, P>(X, v, d, ln, s);
     m = Real(0);
     p = Real(0);
 #pragma unroll
@@ -377,13 +469,52 @@ __device__ __forceinline__ void warp_stage(Real* s, const Real* g, int lane) {
     }
 }
 
-// trace of variable v on face (d, side) at face point fp
+// as warp_stage, choosing 16-byte chunks at run time when the shared side
+// allows them (SVEC) and the global address is 16-byte aligned
+template <int N, bool SVEC, typename Real>
+__device__ __forceinline__ void warp_stage_auto(Real* s, const Real* g, int lane) {
+    constexpr bool V = SVEC && (N * sizeof(Real)) % 16 == 0;
+    if (V && (reinterpret_cast<uintptr_t>(g) & 15u) == 0)
+        warp_stage<N, V>(s, g, lane);
+    else
+        warp_stage<N, false>(s, g, lane);
+}
+
+// stage one element's state [NV][NSP] (canonical global layout) into the
+// volume placement; rows go as 16-byte copies when the global rows are aligned
 template <int DIM, int P, typename Real>
-__device__ __forceinline__ Real trace_of(const Real* sv, const Ops<Real>& op, int d, int side, int fp) {
-    constexpr int NP = P + 1;
+__device__ __forceinline__ void warp_stage_vol(Real* s, const Real* g, int lane) {
+    using V = Vol<DIM, P, Real>;
+    constexpr int NV = DIM + 2, NP = P + 1, NSP = V::NSP;
+    if constexpr (V::ROW4) {
+        if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
+            constexpr int NR = NV * NSP / NP;   // rows
+            for (int k = lane; k < NR; k += 32) {
+                const int v = k / (NSP / NP), r = k % (NSP / NP);
+                cp_async16(s + V::at(v, 0, r % NP, r / NP), g + k * NP);
+            }
+            return;
+        }
+    }
+    for (int k = lane; k < NV * NSP; k += 32)
+        cp_async_small<int(sizeof(Real))>(s + V::pt(k / NSP, k % NSP), g + k);
+}
+
+// trace on face (d, side) at face point fp of variable v of volume array X:
+// sum over the line's points j of c[j] X_j, where c holds l_j(-1) (side 0) or
+// l_j(+1) (side 1), selected once per face point by face_coefs
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ void face_coefs(const Ops<Real>& op, int side, Real (&c)[P + 1]) {
+#pragma unroll
+    for (int j = 0; j < P + 1; ++j) c[j] = side ? op.lm[P - j] : op.lm[j];
+}
+template <int DIM, int P, typename Real>
+__device__ __forceinline__ Real trace_at(const Real* X, int v, int d, int fp, const Real (&c)[P + 1]) {
+    Real s[P + 1];
+    vload_line<DIM, P>(X, v, d, fp, s);
     Real acc = Real(0);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc += op.lm[j] * sv[line_sp<DIM, NP>(d, fp, side ? NP - 1 - j : j)];
+    for (int j = 0; j < P + 1; ++j) acc += c[j] * s[j];
     return acc;
 }
 
@@ -393,15 +524,18 @@ template <int DIM, int P, typename Real>
 __device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restrict__ ufe, const Ops<Real>& op,
                                                   int lane) {
     using Z = Sz<DIM, P>;
-    constexpr int NSP = Z::NSP, NFP = Z::NFP, NV = Z::NV;
+    constexpr int NFP = Z::NFP, NV = Z::NV;
+    constexpr int NL = NV * NFP, NLI = (NL + 31) / 32;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < NV * NFP; t += 32) {
-            const int v = t / NFP, ln = t % NFP;
+#pragma unroll 1
+        for (int it = 0; it < NLI; ++it) {
+            const LineTask<DIM, P> tk(lane, it);
+            if (NL % 32 != 0 && tk.t >= NL) break;
             Real m, p;
-            line_ends<DIM, P>(su + v * NSP, op, d, ln, m, p);
-            ufe[2 * d * NV * NFP + t] = m;
-            ufe[(2 * d + 1) * NV * NFP + t] = p;
+            line_ends<DIM, P>(su + tk.shift, tk.vref, op, d, tk.ln, m, p);
+            ufe[2 * d * NV * NFP + tk.t] = m;
+            ufe[(2 * d + 1) * NV * NFP + tk.t] = p;
         }
     }
 }
@@ -418,7 +552,9 @@ __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int6
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (e >= E) return;
     Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::traces;
-    warp_load<NV * NSP, Smem<DIM, P>::traces>(u + e * NV * NSP, su, lane);
+    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncwarp();
     warp_write_traces<DIM, P>(su, uf + e * NF * NV * NFP, op, lane);
 }
@@ -432,16 +568,23 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                             const __grid_constant__ Geo<Real> g) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    constexpr int NSPW = (NSP + 31) / 32;           // solution points per lane
+    constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
+    constexpr int NLI = (NL + 31) / 32;             // ... per lane
+    constexpr int NFI = (2 * NFP + 31) / 32;        // face points of one direction per lane
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (e >= E) return;
     using SM = Smem<DIM, P>;
-    Real* su = reinterpret_cast<Real*>(smem) + warp * SM::visc;
+    using VL = Vol<DIM, P, Real>;
+    const bool curved = g.sS_sp != 0;               // per-point metrics, staged after region D
+    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc);
     Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
     Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
     Real* sg = su + SM::vD;              // gradient          [d or i][v][sp]
     Real* sn = sg;                       // staged neighbour traces [f][v][fp] (face phase only)
+    Real* sS = su + SM::visc;            // curved: S [k][sp], 1/|J| [sp]
     // face codes of this element, broadcast to every lane
     int codes[NF];
     {
@@ -449,28 +592,34 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
-    // stage the element state and the neighbours' face traces (two groups)
-    constexpr bool VS = (SM::visc * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
-                        (SM::vD * sizeof(Real)) % 16 == 0;
-    constexpr bool VU = (SM::visc * sizeof(Real)) % 16 == 0 && (NV * NSP * sizeof(Real)) % 16 == 0;
-    if (VU && (reinterpret_cast<uintptr_t>(u + e * NV * NSP) & 15u) == 0)
-        warp_stage<NV * NSP, VU>(su, u + e * NV * NSP, lane);
-    else
-        warp_stage<NV * NSP, false>(su, u + e * NV * NSP, lane);
+    // stage the element state, the neighbours' face traces and (curved) the
+    // metrics, in three groups
+    constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0;
+    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0;
+    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
     cp_async_commit();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
         if (codes[f] >= 0) warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
     cp_async_commit();
-    cp_async_wait<1>();
+    if (curved) {
+        warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane);
+        warp_stage_auto<NSP, VW && ((SM::visc + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
+            sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane);
+    }
+    cp_async_commit();
+    cp_async_wait<2>();
     __syncwarp();
     // B: own traces (line pass), then neighbour traces and jumps per face point
     warp_write_traces<DIM, P>(su, sl, op, lane);
-    cp_async_wait<0>();
+    cp_async_wait<1>();
     __syncwarp();
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < 2 * NFP; t += 32) {
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = lane + 32 * it;
+            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
@@ -496,31 +645,43 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < NV * NFP; t += 32) {
-            const int v = t / NFP, ln = t % NFP;
-            Real s[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) s[j] = su[v * NSP + line_sp<DIM, NP>(d, ln, j)];
+#pragma unroll 1
+        for (int it = 0; it < NLI; ++it) {
+            const LineTask<DIM, P> tk(lane, it);
+            if (NL % 32 != 0 && tk.t >= NL) break;
+            Real s[NP], q[NP];
+            vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                Real q = Real(0);
+                q[i] = Real(0);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) q += op.D[i * MAXNP + j] * s[j];
-                sg[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, i)] = q;
+                for (int j = 0; j < NP; ++j) q[i] += op.D[i * MAXNP + j] * s[j];
             }
+            vstore_line<DIM, P>(sg + tk.shift, d * NV + tk.vref, d, tk.ln, q);
         }
     }
+    cp_async_wait<0>();
     __syncwarp();
     // C2: physical gradient (1/|J|) S^T q at each solution point, in place
-    for (int sp = lane; sp < NSP; sp += 32) {
+#pragma unroll 1
+    for (int s = 0; s < NSPW; ++s) {
+        const int sp = lane + 32 * s;
+        if (NSP % 32 != 0 && sp >= NSP) break;
         Real q[DIM][NV];
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) q[d][v] = sg[(d * NV + v) * NSP + sp];
+            for (int v = 0; v < NV; ++v) q[d][v] = sg[VL::pt(d * NV + v, sp)];
         Real S[DIM * DIM];
-        load_S<DIM>(g, e, sp, S);
-        const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
+        Real iJ;
+        if (curved) {
+#pragma unroll
+            for (int k = 0; k < DIM * DIM; ++k) S[k] = sS[k * NSP + sp];
+            iJ = sS[DIM * DIM * NSP + sp];
+        } else {
+            load_S<DIM>(g, e, 0, S);
+            iJ = g.iJ[e * g.sJ_e];
+        }
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
@@ -528,21 +689,36 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 Real acc = Real(0);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
-                sg[(i * NV + v) * NSP + sp] = acc * iJ;
+                sg[VL::pt(i * NV + v, sp)] = acc * iJ;
             }
     }
+    // normals of this lane's face points, all directions at once
+    Real Nr[DIM][NFI][DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = lane + 32 * it;
+            const int side = t >= NFP ? 1 : 0;
+            if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
+        }
     __syncwarp();
     // D: lifted face gradient, viscous normal flux
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < 2 * NFP; t += 32) {
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = lane + 32 * it;
+            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
             const Real nsg = side ? Real(1) : Real(-1);
+            Real cf[NP];
+            face_coefs<DIM, P>(op, side, cf);
             // lifting coefficient along the line: nsign sum_j l_j h_j S_j[d][i] / J_j
             Real lc[DIM];
-            if (g.sS_sp == 0 && g.sJ_sp == 0) {
+            if (!curved) {
                 const Real iJ = g.iJ[e * g.sJ_e];
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) lc[i] = nsg * op.lhm * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
@@ -551,11 +727,12 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 for (int i = 0; i < DIM; ++i) lc[i] = Real(0);
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    const int sp = line_sp<DIM, NP>(d, fp, side ? NP - 1 - j : j);
-                    const Real c = op.lm[j] * op.hm[j] * g.iJ[e * g.sJ_e + sp * g.sJ_sp];
+                    // point j of the line; weight l(x_j) h(x_j) of its own end
+                    const int sp = line_sp<DIM, NP>(d, fp, j);
+                    const Real w = side ? op.lm[NP - 1 - j] * op.hm[NP - 1 - j] : op.lm[j] * op.hm[j];
+                    const Real c = w * sS[DIM * DIM * NSP + sp];
 #pragma unroll
-                    for (int i = 0; i < DIM; ++i)
-                        lc[i] += c * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k + sp * g.sS_sp];
+                    for (int i = 0; i < DIM; ++i) lc[i] += c * sS[(d * DIM + i) * NSP + sp];
                 }
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
@@ -568,10 +745,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 uL[v] = sl[(f * NV + v) * NFP + fp];
 #pragma unroll
                 for (int i = 0; i < DIM; ++i)
-                    G[v][i] = trace_of<DIM, P>(sg + (i * NV + v) * NSP, op, d, side, fp) + ph.eta * lc[i] * jv;
+                    G[v][i] = trace_at<DIM, P>(sg, i * NV + v, d, fp, cf) + ph.eta * lc[i] * jv;
             }
-            Real N[DIM];
-            load_normal<DIM>(g, e, f, fp, N);
+            const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             Real Fv[NV][DIM];
             if (code >= 0) {
@@ -598,28 +774,34 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 // correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
 // stages) the traces of the updated state written for the next stage.
 template <int DIM, int P, typename Real>
-__global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
+__global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
                            const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
                            const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
                            const __grid_constant__ Stage<Real> st) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
     constexpr int NSPW = (NSP + 31) / 32;           // solution points per lane
+    constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
+    constexpr int NLI = (NL + 31) / 32;             // ... per lane
+    constexpr int NFI = (2 * NFP + 31) / 32;        // face points of one direction per lane
     constexpr bool PREFETCH = NSPW <= 2;            // RK arrays held in registers
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
     if (e >= E) return;
     using SM = Smem<DIM, P>;
-    Real* su = reinterpret_cast<Real*>(smem) + warp * SM::resid;
+    using VL = Vol<DIM, P, Real>;
+    const bool curved = g.sS_sp != 0;               // per-point metrics, staged in region E
+    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::resid_c : SM::resid);
     Real* sj = su + SM::rB;              // jumps u_c - u_f      [f][v][fp]
     Real* sd = sj;                       // divergence [v][sp], after the gradient
-    Real* sc = su + SM::rC;              // Fc.N, then Fc.N - own [f][v][fp]
+    Real* sc = su + SM::rC;              // Fc.N - own viscous flux [f][v][fp]
     Real* sF = su + SM::rD;              // own/neighbour traces, q_d, then F~_d  [d][v][sp]
     Real* sl = sF;                       // own traces            [f][v][fp]  (face phase)
     Real* sn = sF + NF * NV * NFP;       // neighbour traces      [f][v][fp]  (face phase)
     Real* so = sc;                       // own viscous fluxes    [f][v][fp]  (face phase)
     Real* sm = su + SM::rE;              // neighbour viscous fluxes [f][v][fp] (face phase)
+    Real* sg = sm;                       // curved: S [k][sp], 1/|J| [sp] (after the face phase)
     const int64_t base = e * NV * NSP;
     int codes[NF];
     {
@@ -627,14 +809,10 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
-    constexpr bool VS = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
-                        (SM::rC * sizeof(Real)) % 16 == 0 && (SM::rD * sizeof(Real)) % 16 == 0 &&
-                        (SM::rE * sizeof(Real)) % 16 == 0;
-    constexpr bool VU = (SM::resid * sizeof(Real)) % 16 == 0 && (NV * NSP * sizeof(Real)) % 16 == 0;
-    if (VU && (reinterpret_cast<uintptr_t>(u + base) & 15u) == 0)
-        warp_stage<NV * NSP, VU>(su, u + base, lane);
-    else
-        warp_stage<NV * NSP, false>(su, u + base, lane);
+    constexpr bool VW = (SM::resid * sizeof(Real)) % 16 == 0 && (SM::resid_c * sizeof(Real)) % 16 == 0;
+    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::rC * sizeof(Real)) % 16 == 0 &&
+                        (SM::rD * sizeof(Real)) % 16 == 0 && (SM::rE * sizeof(Real)) % 16 == 0;
+    warp_stage_vol<DIM, P>(su, u + base, lane);
     cp_async_commit();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
@@ -645,7 +823,17 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
         }
     if (ph.viscous) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane);
     cp_async_commit();
-    // the RK stage arrays are only needed at the end: issue their loads now
+    // face normals of this lane's face points, and the RK stage arrays (needed
+    // only at the end): issue their loads now
+    Real Nr[DIM][NFI][DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = lane + 32 * it;
+            const int side = t >= NFP ? 1 : 0;
+            if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
+        }
     Real pu0[NSPW][NV], pacc[NSPW][NV];
     if constexpr (PREFETCH) {
         if (st.stage >= 2) {
@@ -670,15 +858,17 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
     // B: common normal flux (Rusanov minus common viscous) and jumps
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < 2 * NFP; t += 32) {
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = lane + 32 * it;
+            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
             Real uL[NV], uR[NV], uc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
-            Real N[DIM];
-            load_normal<DIM>(g, e, f, fp, N);
+            const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             int fpn = 0;
             if (code >= 0) {
@@ -713,36 +903,54 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
         }
     }
     __syncwarp();
+    // curved meshes: stage S and 1/|J| into region E (free after the face
+    // phase); the copy overlaps the gradient pass
+    if (curved) {
+        warp_stage_auto<DIM * DIM * NSP, VW && (SM::rE * sizeof(Real)) % 16 == 0>(sg, g.S + e * g.sS_e, lane);
+        warp_stage_auto<NSP, VW && ((SM::rE + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
+            sg + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane);
+        cp_async_commit();
+    }
     // C1 (viscous): corrected reference gradient along lines,
     // q_d = D_d u + nsign h_f (u_c - u_f) for the two faces normal to d
     if (ph.viscous) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            for (int t = lane; t < NV * NFP; t += 32) {
-                const int v = t / NFP, ln = t % NFP;
-                Real s[NP];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) s[j] = su[v * NSP + line_sp<DIM, NP>(d, ln, j)];
-                const Real jL = sj[((2 * d) * NV + v) * NFP + ln];
-                const Real jR = sj[((2 * d + 1) * NV + v) * NFP + ln];
+#pragma unroll 1
+            for (int it = 0; it < NLI; ++it) {
+                const LineTask<DIM, P> tk(lane, it);
+                if (NL % 32 != 0 && tk.t >= NL) break;
+                Real s[NP], q[NP];
+                vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
+                const Real jL = sj[2 * d * NV * NFP + tk.t];
+                const Real jR = sj[(2 * d + 1) * NV * NFP + tk.t];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    Real q = op.hm[NP - 1 - i] * jR - op.hm[i] * jL;
+                    q[i] = op.hm[NP - 1 - i] * jR - op.hm[i] * jL;
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) q += op.D[i * MAXNP + j] * s[j];
-                    sF[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, i)] = q;
+                    for (int j = 0; j < NP; ++j) q[i] += op.D[i * MAXNP + j] * s[j];
                 }
+                vstore_line<DIM, P>(sF + tk.shift, d * NV + tk.vref, d, tk.ln, q);
             }
         }
-        __syncwarp();
     }
+    if (curved) cp_async_wait<0>();
+    __syncwarp();
     // C2: flux at solution points, F~_d = sum_i S[d][i] (F_inv - F_vis)_i
-    for (int sp = lane; sp < NSP; sp += 32) {
+#pragma unroll 1
+    for (int s = 0; s < NSPW; ++s) {
+        const int sp = lane + 32 * s;
+        if (NSP % 32 != 0 && sp >= NSP) break;
         Real uu[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uu[v] = su[v * NSP + sp];
+        for (int v = 0; v < NV; ++v) uu[v] = su[VL::pt(v, sp)];
         Real S[DIM * DIM];
-        load_S<DIM>(g, e, sp, S);
+        if (curved) {
+#pragma unroll
+            for (int k = 0; k < DIM * DIM; ++k) S[k] = sg[k * NSP + sp];
+        } else {
+            load_S<DIM>(g, e, 0, S);
+        }
         Real F[NV][DIM];
         const Real ir = Real(1) / uu[0];
         Real m2 = Real(0);
@@ -758,7 +966,7 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
             F[NV - 1][j] = (uu[NV - 1] + p) * vj;
         }
         if (ph.viscous) {
-            const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
+            const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
             Real G[NV][DIM];
 #pragma unroll
             for (int v = 0; v < NV; ++v)
@@ -766,7 +974,7 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                 for (int i = 0; i < DIM; ++i) {
                     Real acc = Real(0);
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * sF[(d * NV + v) * NSP + sp];
+                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * sF[VL::pt(d * NV + v, sp)];
                     G[v][i] = acc * iJ;
                 }
             Real Fv[NV][DIM];
@@ -783,40 +991,43 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
                 Real acc = Real(0);
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];
-                sF[(d * NV + v) * NSP + sp] = acc;
+                sF[VL::pt(d * NV + v, sp)] = acc;
             }
     }
     __syncwarp();
-    // D: flux jump at both faces of each line, Fc.N - nsign I_f[F~_d]
+    // D+E: per line of direction d, the flux jumps at both ends,
+    // Fc.N - nsign I_f[F~_d], and the divergence plus correction, accumulated
+    // direction by direction
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < NV * NFP; t += 32) {
-            const int v = t / NFP, ln = t % NFP;
-            Real m, pp;
-            line_ends<DIM, P>(sF + (d * NV + v) * NSP, op, d, ln, m, pp);
-            sc[2 * d * NV * NFP + t] += m;
-            sc[(2 * d + 1) * NV * NFP + t] -= pp;
-        }
-    }
-    __syncwarp();
-    // E: divergence plus correction along lines, accumulated direction by direction
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        for (int t = lane; t < NV * NFP; t += 32) {
-            const int v = t / NFP, ln = t % NFP;
+#pragma unroll 1
+        for (int it = 0; it < NLI; ++it) {
+            const LineTask<DIM, P> tk(lane, it);
+            if (NL % 32 != 0 && tk.t >= NL) break;
             Real s[NP];
+            vload_line<DIM, P>(sF + tk.shift, d * NV + tk.vref, d, tk.ln, s);
+            Real m = Real(0), pp = Real(0);
 #pragma unroll
-            for (int j = 0; j < NP; ++j) s[j] = sF[(d * NV + v) * NSP + line_sp<DIM, NP>(d, ln, j)];
-            const Real cL = sc[((2 * d) * NV + v) * NFP + ln];
-            const Real cR = sc[((2 * d + 1) * NV + v) * NFP + ln];
+            for (int j = 0; j < NP; ++j) {
+                m += op.lm[j] * s[j];
+                pp += op.lm[NP - 1 - j] * s[j];
+            }
+            const Real cL = sc[2 * d * NV * NFP + tk.t] + m;
+            const Real cR = sc[(2 * d + 1) * NV * NFP + tk.t] - pp;
+            Real val[NP];
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                Real val = op.hm[i] * cL + op.hm[NP - 1 - i] * cR;
+                val[i] = op.hm[i] * cL + op.hm[NP - 1 - i] * cR;
 #pragma unroll
-                for (int j = 0; j < NP; ++j) val += op.D[i * MAXNP + j] * s[j];
-                const int k = v * NSP + line_sp<DIM, NP>(d, ln, i);
-                sd[k] = (d == 0) ? val : sd[k] + val;
+                for (int j = 0; j < NP; ++j) val[i] += op.D[i * MAXNP + j] * s[j];
             }
+            if (d > 0) {
+                Real prev[NP];
+                vload_line<DIM, P>(sd + tk.shift, tk.vref, d, tk.ln, prev);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) val[i] += prev[i];
+            }
+            vstore_line<DIM, P>(sd + tk.shift, tk.vref, d, tk.ln, val);
         }
         __syncwarp();
     }
@@ -826,13 +1037,13 @@ __global__ void k_residual(const Real* __restrict__ u, const Real* __restrict__ 
 #pragma unroll
     for (int s = 0; s < NSPW; ++s) {
         const int sp = lane + 32 * s;
-        if (sp >= NSP) break;
-        const Real iJ = g.iJ[e * g.sJ_e + sp * g.sJ_sp];
+        if (NSP % 32 != 0 && sp >= NSP) break;
+        const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const int k = v * NSP + sp;
+            const int k = VL::pt(v, sp);
             const Real r = -sd[k] * iJ;
-            const int64_t gi = base + k;
+            const int64_t gi = base + v * NSP + sp;
             Real u0v = Real(0), accv = Real(0);
             if (st.stage >= 2) {
                 if constexpr (PREFETCH) {
@@ -1020,24 +1231,24 @@ __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t
          w += int64_t(gridDim.x) * blockDim.x) {
         const int64_t e = e_first + w / NSP;
         const int sp = int(w % NSP);
-        double w0 = 0.0, w1 = 0.0, w2 = 1.0;
+        // point values in the working precision, sums in double
+        Real w0 = Real(0), w1 = Real(0), w2 = Real(1);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            if (sp % NP == j) w0 = double(op.w[j]);
-            if ((sp / NP) % NP == j) w1 = double(op.w[j]);
-            if (DIM == 3 && sp / (NP * NP) == j) w2 = double(op.w[j]);
+            if (sp % NP == j) w0 = op.w[j];
+            if ((sp / NP) % NP == j) w1 = op.w[j];
+            if (DIM == 3 && sp / (NP * NP) == j) w2 = op.w[j];
         }
-        double wt = w0 * w1 * w2;
-        wt *= double(g.J[e * g.sJ_e + sp * g.sJ_sp]);  // integrals use |J| itself
+        const Real wt = w0 * w1 * w2 * g.J[e * g.sJ_e + sp * g.sJ_sp];  // integrals use |J| itself
         const Real* ue = u + e * NV * NSP + sp;
-        double m2 = 0.0;
+        Real m2 = Real(0);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const double x = double(ue[v * NSP]);
-            acc[v] += wt * x;
+            const Real x = ue[v * NSP];
+            acc[v] += double(wt * x);
             if (v >= 1 && v <= DIM) m2 += x * x;
         }
-        acc[NV] += wt * 0.5 * m2 / double(ue[0]);
+        acc[NV] += double(wt * Real(0.5) * m2 / ue[0]);
     }
 #pragma unroll
     for (int v = 0; v <= NV; ++v) red[v][threadIdx.x] = acc[v];

@@ -39,7 +39,7 @@ template <int P>
 int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>& op,
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_visc_face<FR_DIM, P, FR_REAL>;
-    const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb);
+    const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
@@ -53,7 +53,7 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_residual<FR_DIM, P, FR_REAL>;
-    const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb);
+    const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
@@ -104,10 +104,10 @@ int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const 
 }
 
 template <>
-size_t smem_bytes<FR_REAL, FR_DIM>(int P, int kernel, int epb) {
-#define C(PP) (kernel == 0 ? frk::smem_traces<FR_DIM, PP, FR_REAL>(epb) \
-               : kernel == 1 ? frk::smem_visc<FR_DIM, PP, FR_REAL>(epb)  \
-                             : frk::smem_resid<FR_DIM, PP, FR_REAL>(epb))
+size_t smem_bytes<FR_REAL, FR_DIM>(int P, int kernel, int epb, bool curved) {
+#define C(PP) (kernel == 0 ? frk::smem_traces<FR_DIM, PP, FR_REAL>(epb)          \
+               : kernel == 1 ? frk::smem_visc<FR_DIM, PP, FR_REAL>(epb, curved)  \
+                             : frk::smem_resid<FR_DIM, PP, FR_REAL>(epb, curved))
     switch (P) {
         case 1: return C(1);
         case 2: return C(2);
