@@ -126,6 +126,40 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ----------------------------------------------------------------------------- ncu counters
+KERNEL_SOURCES = ("fr_kernels.cuh", "fr_common.h", "fr_launch.cuh", "fr_f32_3d.cu", "fr_f64_3d.cu")
+
+
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the kernel sources: counters taken on
+    other sources are stale and are not reported."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2501_05709_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_counter(workload, precision, kernel, key):
+    """A per-launch figure from profiles/ncu_counters.txt (written from one ncu
+    capture of this script), or None when it was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_counters.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = kernel_source_hash()
+    for ln in lines:
+        if ln.startswith("#") or "=" not in ln:
+            continue
+        kv = dict(t.split("=", 1) for t in ln.split())
+        if (kv.get("src") == src and kv.get("workload") == workload and kv.get("precision") == precision
+                and kv.get("kernel") == kernel and key in kv):
+            return float(kv[key])
+    return None
+
+
 # ----------------------------------------------------------------------------- GPU leg
 def algorithmic_bytes(E, p, rsz, viscous=True, dim=3, curved=False):
     """Minimum HBM bytes per RK stage of each kernel: every array the kernel
@@ -327,19 +361,46 @@ def gpu_leg(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         ms64 = max_over_ranks(a.elapsed_time(b))
-        F.fr_rk_step_graph(c64, args.steps, sh)  # same step count as the FP32 state
+        # per-kernel times over the same number of steps as the FP32 leg's
+        # profile, which also brings the FP64 state to the FP32 state's step
+        kms64, kn64 = F.fr_profile_step(c64, args.steps, sh)
+        dfma_peak = F.fr_probe_fp64_peak(sh)
         u64 = F.fr_state_get(c64)
         dev = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
         ke = F.fr_integrals(c64)[-1]
         c64.close()
         fp64 = {"value": world * dof * 4 * args.steps / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / args.steps,
                 "fp32_state_rel_l2_vs_fp64": dev, "steps_compared": steps_done, "ke_fp64": ke}
+        # FP64 kernels are bound by the FP64 pipe: executed FP64 flops per
+        # launch (ncu: 2 DFMA + DADD + DMUL, stage average) against the DFMA
+        # rate measured on this GPU
+        r64 = kms64[2] / max(kn64[2], 1)
+        fl = ncu_counter(args.workload, "fp64", "k_residual", "fp64_flops_per_launch")
+        ach = fl / (r64 / 1e3) / 1e9 if fl else None
+        fp64["roofline"] = {"bound": "alu", "kernel": "k_residual (FR residual + RK4 stage), FP64",
+                            "achieved": ach, "peak": dfma_peak, "unit": "GFLOP/s",
+                            "frac": ach / dfma_peak if ach else None,
+                            "peak_source": "measured: FP64 FMA throughput probe (fr_probe_fp64_peak) on this GPU",
+                            "flops_per_launch": fl, "avg_launch_ms": r64,
+                            "traffic": ncu_counter(args.workload, "fp64", "k_residual", "dram_bytes_per_launch")}
+    roof = {"bound": "hbm", "kernel": "k_residual (FR residual + RK4 stage)", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": ncu_counter(args.workload, args.precision, "k_residual", "dram_bytes_per_launch"),
+            "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": ab["resid"]}
+    if prec == F.FR_FP64:
+        # the FP64 kernels are bound by the FP64 pipe (see the fp64 leg below)
+        pk = F.fr_probe_fp64_peak(sh)
+        fl = ncu_counter(args.workload, "fp64", "k_residual", "fp64_flops_per_launch")
+        ach = fl / (resid_ms / 1e3) / 1e9 if fl else None
+        roof = {"bound": "alu", "kernel": "k_residual (FR residual + RK4 stage), FP64", "achieved": ach, "peak": pk,
+                "unit": "GFLOP/s", "frac": ach / pk if ach else None,
+                "traffic": roof["traffic"],
+                "peak_source": "measured: FP64 FMA throughput probe (fr_probe_fp64_peak) on this GPU",
+                "flops_per_launch": fl}
     return {
         "value": value, "ms": ms, "launches": launches, "clocks": ck, "kernels": kernels, "tile_epb": tile,
-        "roofline": {"bound": "hbm", "kernel": "k_residual (FR residual + RK4 stage)", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "algorithmic_bytes_per_launch": ab["resid"]},
+        "roofline": roof,
         "e2e": e2e, "fp64": fp64, "dof": dof, "elements": E,
     }
 

@@ -68,7 +68,7 @@ struct fr_ctx {
     int32_t* wall_ef = nullptr;
     int64_t* wall_off_d = nullptr;
     std::vector<int64_t> wall_off;
-    double *fnow = nullptr, *fsum = nullptr, *fcnt = nullptr, *partial = nullptr;
+    double *fnow = nullptr, *fsum = nullptr, *fcnt = nullptr, *partial = nullptr, *fpart = nullptr;
     int partial_blocks = 0;
     std::vector<Surface> surf;
     frk::Launch lc[3]{};
@@ -184,11 +184,11 @@ int L_forces(fr_ctx* c, cudaStream_t s) {
     ++c->launches;
     return c->dim == 2
                ? frl::forces<Real, 2>(c->p, static_cast<const Real*>(c->ufb[0]), static_cast<const Real*>(c->fvn),
-                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
-                                      c->fsum, c->fcnt, s)
+                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fpart,
+                                      c->fnow, c->fsum, c->fcnt, s)
                : frl::forces<Real, 3>(c->p, static_cast<const Real*>(c->ufb[0]), static_cast<const Real*>(c->fvn),
-                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fnow,
-                                      c->fsum, c->fcnt, s);
+                                      c->wall_ef, c->wall_off_d, c->ncand, op, g, gm1, c->visc, c->fpart,
+                                      c->fnow, c->fsum, c->fcnt, s);
 }
 
 template <typename Real>
@@ -361,7 +361,8 @@ size_t smem_of(const fr_ctx* c, int kernel, int epb) {
 void release(fr_ctx* c) {
     if (!c) return;
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
-                    c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte};
+                    c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
+                    c->fpart};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -657,7 +658,8 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
     if (cudaMalloc(&c->fnow, sizeof(double) * 3 * ncand) != cudaSuccess ||
         cudaMalloc(&c->fsum, sizeof(double) * 3 * ncand) != cudaSuccess ||
         cudaMalloc(&c->fcnt, sizeof(double) * ncand) != cudaSuccess ||
-        cudaMalloc(&c->partial, sizeof(double) * c->partial_blocks * (nv + 1)) != cudaSuccess) {
+        cudaMalloc(&c->partial, sizeof(double) * c->partial_blocks * (nv + 1)) != cudaSuccess ||
+        cudaMalloc(&c->fpart, sizeof(double) * 3 * frk::FORCE_BLOCKS * ncand) != cudaSuccess) {
         release(c);
         return fail(FR_ENOMEM, "cudaMalloc failed for accumulators");
     }

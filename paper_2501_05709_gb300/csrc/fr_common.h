@@ -10,6 +10,7 @@
 namespace frk {
 
 constexpr int MAXNP = 5;  // p <= 4
+constexpr int FORCE_BLOCKS = 64;  // wall-force partial sums per candidate
 
 // 1D reference operators of one order p and correction kind, Section 1 (FR):
 // lm/lp extrapolate a line of solution points to the xi=-1/+1 end, D is the
@@ -104,7 +105,7 @@ int residual(int P, const Real* u, const Real* uf, const Real* fvn, int64_t E,
 template <typename Real, int DIM>
 int forces(int P, const Real* uf, const Real* fvn, const int32_t* wall_ef, const int64_t* wall_off,
            int ncand, const frk::Ops<Real>& op, const frk::Geo<Real>& g, Real gm1, int viscous,
-           double* fnow, double* fsum, double* fcnt, void* stream);
+           double* part, double* fnow, double* fsum, double* fcnt, void* stream);
 
 // count: device int[3] = records, steps seen, overflow flag
 template <typename Real, int DIM>

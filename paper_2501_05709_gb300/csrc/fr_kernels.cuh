@@ -1089,26 +1089,28 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     }
 }
 
-// Wall force (Section 3.2): one block per candidate sums, over that
-// candidate's wall face points, w_fp (p N - tau.N) with N the element's
-// outward area-weighted normal (into the body), p from the interior trace and
-// tau.N the momentum entries of the wall's common viscous flux.  Accumulated
-// in double; fnow/fsum/fcnt are updated in place (graph-replay safe).
+// Wall force (Section 3.2): FORCE_BLOCKS blocks per candidate each sum, over
+// a slice of that candidate's wall face points, w_fp (p N - tau.N) with N the
+// element's outward area-weighted normal (into the body), p from the interior
+// trace and tau.N the momentum entries of the wall's common viscous flux, in
+// double, into part[c][block][DIM]; k_forces_fin adds the partial sums in a
+// fixed order (deterministic) and updates fnow/fsum/fcnt in place
+// (graph-replay safe).
 template <int DIM, int P, typename Real>
 __global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ fvn,
                          const int32_t* __restrict__ wall_ef, const int64_t* __restrict__ wall_off,
                          const __grid_constant__ Ops<Real> op, const __grid_constant__ Geo<Real> g, Real gm1,
-                         int viscous,
-                         double* __restrict__ fnow, double* __restrict__ fsum, double* __restrict__ fcnt) {
+                         int viscous, double* __restrict__ part) {
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
     __shared__ double red[DIM][256];
-    const int c = blockIdx.x;
+    const int c = blockIdx.y;
     const int64_t b = wall_off[c], n = wall_off[c + 1] - b;
     double acc[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) acc[i] = 0.0;
-    for (int64_t w = threadIdx.x; w < n * NFP; w += blockDim.x) {
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < n * NFP;
+         w += int64_t(gridDim.x) * blockDim.x) {
         const int fp = int(w % NFP);
         const int32_t ef = wall_ef[b + w / NFP];
         const int64_t e = ef / NF;
@@ -1149,11 +1151,29 @@ __global__ void k_forces(const Real* __restrict__ uf, const Real* __restrict__ f
             for (int i = 0; i < DIM; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-            fnow[c * 3 + i] = red[i][0];
-            fsum[c * 3 + i] += red[i][0];
+        for (int i = 0; i < DIM; ++i) part[(int64_t(c) * gridDim.x + blockIdx.x) * 3 + i] = red[i][0];
+}
+
+// one warp per candidate: lane l adds partial sums l, l+32, ..., then a fixed
+// butterfly adds the lanes (the same order on every call)
+static __global__ void k_forces_fin(const double* __restrict__ part, int nblk, double* __restrict__ fnow,
+                                    double* __restrict__ fsum, double* __restrict__ fcnt) {
+    const int c = blockIdx.x, lane = threadIdx.x & 31;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < nblk; k += 32)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[i] += part[(int64_t(c) * nblk + k) * 3 + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            fnow[c * 3 + i] = s[i];
+            fsum[c * 3 + i] += s[i];
         }
         fcnt[c] += 1.0;
     }
@@ -1224,14 +1244,14 @@ __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t
     using Z = Sz<DIM, P>;
     constexpr int NP = Z::NP, NSP = Z::NSP, NV = Z::NV;
     __shared__ double red[NV + 1][256];
-    double acc[NV + 1];
+    // each thread sums its points in the working precision, blocks in double
+    Real acc[NV + 1];
 #pragma unroll
-    for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+    for (int v = 0; v <= NV; ++v) acc[v] = Real(0);
     for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < ne * NSP;
          w += int64_t(gridDim.x) * blockDim.x) {
         const int64_t e = e_first + w / NSP;
         const int sp = int(w % NSP);
-        // point values in the working precision, sums in double
         Real w0 = Real(0), w1 = Real(0), w2 = Real(1);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -1245,13 +1265,13 @@ __global__ void k_integrals(const Real* __restrict__ u, int64_t e_first, int64_t
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const Real x = ue[v * NSP];
-            acc[v] += double(wt * x);
+            acc[v] += wt * x;
             if (v >= 1 && v <= DIM) m2 += x * x;
         }
-        acc[NV] += double(wt * Real(0.5) * m2 / ue[0]);
+        acc[NV] += wt * Real(0.5) * m2 / ue[0];
     }
 #pragma unroll
-    for (int v = 0; v <= NV; ++v) red[v][threadIdx.x] = acc[v];
+    for (int v = 0; v <= NV; ++v) red[v][threadIdx.x] = double(acc[v]);
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st)

@@ -121,12 +121,14 @@ size_t smem_bytes<FR_REAL, FR_DIM>(int P, int kernel, int epb, bool curved) {
 template <>
 int forces<FR_REAL, FR_DIM>(int P, const FR_REAL* uf, const FR_REAL* fvn, const int32_t* wall_ef,
                             const int64_t* wall_off, int ncand, const frk::Ops<FR_REAL>& op,
-                            const frk::Geo<FR_REAL>& g, FR_REAL gm1, int viscous, double* fnow, double* fsum,
-                            double* fcnt, void* stream) {
+                            const frk::Geo<FR_REAL>& g, FR_REAL gm1, int viscous, double* part, double* fnow,
+                            double* fsum, double* fcnt, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (ncand <= 0) return 0;
-#define C(PP) (frk::k_forces<FR_DIM, PP, FR_REAL><<<ncand, 256, 0, s>>>(uf, fvn, wall_ef, wall_off, op, g, gm1, \
-                                                                         viscous, fnow, fsum, fcnt),         \
+    const dim3 grid(frk::FORCE_BLOCKS, unsigned(ncand));
+#define C(PP) (frk::k_forces<FR_DIM, PP, FR_REAL><<<grid, 256, 0, s>>>(uf, fvn, wall_ef, wall_off, op, g, gm1, \
+                                                                        viscous, part),                      \
+               frk::k_forces_fin<<<ncand, 32, 0, s>>>(part, frk::FORCE_BLOCKS, fnow, fsum, fcnt),          \
                int(cudaGetLastError()))
     FR_DISPATCH(C)
 #undef C
