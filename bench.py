@@ -127,16 +127,17 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- ncu counters
-KERNEL_SOURCES = ("fr_kernels.cuh", "fr_common.h", "fr_launch.cuh", "fr_f32_3d.cu", "fr_f64_3d.cu")
+KERNEL_SOURCES = ("csrc/fr_kernels.cuh", "csrc/fr_common.h", "csrc/fr_launch.cuh", "csrc/fr_f32_3d.cu",
+                  "csrc/fr_f64_3d.cu", "build.py")
 
 
 def kernel_source_hash():
-    """sha256 (first 16 hex digits) of the kernel sources: counters taken on
-    other sources are stale and are not reported."""
+    """sha256 (first 16 hex digits) of the kernel sources and build flags:
+    counters taken on other sources are stale and are not reported."""
     import hashlib
     h = hashlib.sha256()
     for n in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2501_05709_gb300", "csrc", n), "rb") as f:
+        with open(os.path.join(ROOT, "paper_2501_05709_gb300", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 

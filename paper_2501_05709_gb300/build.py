@@ -52,7 +52,10 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
-        cmd = [nvcc] + flags + ["-c", src, "-o", obj]
+        # the FP32 kernels use the hardware reciprocal and square root (<= 2 ulp)
+        # and flush denormals; the FP64 kernels keep IEEE division and sqrt
+        extra = ["-use_fast_math"] if os.path.basename(src).startswith("fr_f32") else []
+        cmd = [nvcc] + flags + extra + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", SRC, "-x", "c++",
                    "-c", src, "-o", obj]
