@@ -90,6 +90,33 @@ def run_oracle_subprocess(min_seconds, max_steps=10000, warmup=1):
             "sample": f"TGV p=3 on a 4^3-element box ({dof} DOF), {k} RK4 steps in {dt:.1f} s, numpy FP64, 1 BLAS thread"}
 
 
+def run_oracle_all_cores(min_seconds):
+    """The same oracle sample in one single-threaded process per host core,
+    all at once; value = the sum of their rates (element-parallel work spread
+    over the cores, without changing the oracle)."""
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(min_seconds=%f)))" % (ROOT, min_seconds))
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env) for _ in range(ncores)]
+    rates, steps, secs = [], 0, 0.0
+    for pr in procs:
+        out, err = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        v, k, dt, dof = json.loads(out.strip().splitlines()[-1])
+        rates.append(v)
+        steps += k
+        secs = max(secs, dt)
+    return {"value": float(sum(rates)), "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} concurrent single-threaded processes, each TGV p=3 on a 4^3-element box "
+                      f"({dof} DOF) for >= {min_seconds:.0f} s ({steps} RK4 steps in total), numpy FP64"}
+
+
 # ----------------------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -447,11 +474,16 @@ def main():
     r = gpu_leg(args, rank, world, local_rank)
     if rank == 0:
         cb = None
+        cb_all = None
         if not args.no_cpu_baseline:
             try:
                 cb = run_oracle_subprocess(min_seconds=10.0)
             except Exception as e:  # reported, not fatal
                 cb = {"value": None, "error": str(e)[-300:]}
+            try:
+                cb_all = run_oracle_all_cores(min_seconds=10.0)
+            except Exception as e:
+                cb_all = {"value": None, "error": str(e)[-300:]}
         config["autotuned_elements_per_block"] = r["tile_epb"]
         config["elements"] = r["elements"]
         config["dof_per_variable"] = r["dof"]
@@ -459,7 +491,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                 "data": "synthetic", "config": config, "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
-                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"]}
+                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch
