@@ -433,6 +433,47 @@ def gpu_leg(args, rank, world, local_rank):
     }
 
 
+def fwh_leg():
+    """FW-H post-processing at the directivity scale of Section 3.3: the
+    18,840-panel cylinder of the airfoil workloads, 36 observers on the
+    r = 10c circle, the surface duplicated to 3 spans, a 1000-sample record of
+    a seeded moving-medium monopole field (nondimensional: |V| = 1, M = 0.2,
+    AoA 3 deg); then the Welch PSD of every observer series."""
+    import torch
+
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    y, n, dS = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=0.2)
+    nt, dt, c0, a = 1000, 0.002, 5.0, math.radians(3.0)
+    M = [0.2 * math.cos(a), 0.2 * math.sin(a), 0.0]
+    tau = dt * np.arange(nt)
+    fld = W.monopole_field(y[None], tau[:, None], M, A=1e-3, omega=4 * np.pi, c0=c0, rho0=1.0)
+    hist = np.concatenate([fld["rho"][..., None], fld["vel"], fld["p"][..., None]], axis=-1)
+    ang = np.radians(np.arange(0, 360, 10))
+    obs = np.stack([0.5 + 10.0 * np.cos(ang), 10.0 * np.sin(ang), np.full_like(ang, 0.1)], axis=1)
+    d = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+    hd, yd, nd, sd = d(hist), d(y), d(n), d(dS)
+    args = (hd, yd, nd, sd, dt, 0.0, obs, M, c0, 1.0, fld["p0"])
+    F.fwh_integrate(*args, Lspan=0.2, ncopies=3)           # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p_out, nt_out, _ = F.fwh_integrate(*args, Lspan=0.2, ncopies=3)
+    torch.cuda.synchronize()
+    t_int = time.perf_counter() - t0
+    nmin = int(nt_out.min())
+    F.fwh_psd(p_out, dt, nseg=3, nt=nmin)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F.fwh_psd(p_out, dt, nseg=3, nt=nmin)
+    torch.cuda.synchronize()
+    t_psd = time.perf_counter() - t0
+    work = len(y) * len(obs) * 3 * nt
+    return {"panels": int(len(y)), "observers": int(len(obs)), "copies": 3, "samples": nt,
+            "window_samples_min": nmin, "fwh_integrate_ms": 1e3 * t_int,
+            "panel_observer_copy_samples_per_s": work / t_int, "fwh_psd_ms": 1e3 * t_psd,
+            "note": "host wall time around each call (each call synchronises and includes its scratch set-up)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,6 +482,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fwh", action="store_true", help="skip the FW-H/PSD post-processing timing")
     ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
     ap.add_argument("--workload", default="tgv32_p3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -472,6 +514,12 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     r = gpu_leg(args, rank, world, local_rank)
+    fwh = None
+    if rank == 0 and not args.no_fwh:
+        try:
+            fwh = fwh_leg()
+        except Exception as e:  # reported, not fatal
+            fwh = {"error": str(e)[-300:]}
     if rank == 0:
         cb = None
         cb_all = None
@@ -491,7 +539,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                 "data": "synthetic", "config": config, "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
-                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all}
+                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all, "fwh": fwh}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

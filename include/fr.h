@@ -231,6 +231,25 @@ int fwh_integrate_noalloc(const double* hist, int nt, int npts, const double* y,
                           int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
                           void* stream);
 
+/* fwh_psd: power spectral density of observer pressure series by Welch's
+ * method, as Section 3.3 computes the PSD of the pressure fluctuations (three
+ * Hann windows, 50% overlap; nseg = 3 reproduces it).  Segment length
+ * L = 2 floor(nt / (nseg + 1)), step L/2; periodic Hann window
+ * w_n = (1 - cos(2 pi n / L)) / 2; each segment loses its mean; one-sided
+ * density P_k = c_k |sum_n w_n y_n exp(-2 pi i k n / L)|^2 dt / sum_n w_n^2,
+ * c_k = 2 except c_0 = c_{L/2} = 1, averaged over the segments; frequency of
+ * entry k is k / (L dt), k = 0..L/2.  FP64 throughout.
+ *   p          device, [nobs][ld] doubles; series o is p[o*ld .. o*ld+nt-1]
+ *              (e.g. the p_out of fwh_integrate with ld = its cap)
+ *   psd        device, [nobs][cap] doubles, written for k = 0..L/2
+ *   nfreq_out  host int: L/2 + 1
+ * Errors: FR_EINVAL for null pointers, nobs < 1, nseg < 1, ld < nt, dt <= 0,
+ * L < 2 (record too short) or cap < L/2 + 1; FR_ENOMEM if its scratch
+ * (twiddle table, windowed segments: 16 L + 8 nobs nseg L bytes) cannot be
+ * allocated.  Synchronises the stream before returning. */
+int fwh_psd(const double* p, int nobs, int nt, int ld, double dt, int nseg, double* psd, int cap,
+            int* nfreq_out, void* stream);
+
 /* Elements per thread block used by the residual kernels (0 = built-in
  * default); fr_autotune times the candidates on the current state and keeps
  * the fastest per kernel, returning it in *best. */

@@ -83,6 +83,8 @@ _SIGS = {
                                         C.c_double, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_double,
                                         C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fwh_psd": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_int,
+                          C.POINTER(C.c_int), C.c_void_p]),
     "fr_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
@@ -312,6 +314,23 @@ def fwh_integrate(hist, y, n, dS, dtau, tau0, obs, Minf, c0, rho0, p0, Lspan=0.0
                                _ptr(obs), nobs, _ptr(M), float(c0), float(rho0), float(p0), float(Lspan),
                                int(ncopies), _ptr(p_out), int(cap), _ptr(nt_out), _ptr(t0_out), _stream(stream)))
     return p_out, nt_out, t0_out
+
+
+def fwh_psd(p, dt, nseg=3, nt=None, psd=None, stream=None):
+    """Welch PSD (nseg Hann windows, 50% overlap) of device float64 series
+    p [nobs, ld] (first nt entries of each row).  Returns (psd device tensor
+    [nobs, nfreq], frequencies as a numpy array)."""
+    nobs, ld = int(p.shape[0]), int(p.shape[1])
+    nt = ld if nt is None else int(nt)
+    cap = 2 * (nt // (nseg + 1)) // 2 + 1
+    if psd is None:
+        import torch
+        psd = torch.zeros((nobs, max(cap, 1)), dtype=torch.float64, device=p.device)
+    nf = C.c_int()
+    _check(lib().fwh_psd(_ptr(p), nobs, nt, ld, float(dt), int(nseg), _ptr(psd), int(psd.shape[1]), C.byref(nf),
+                         _stream(stream)))
+    L = 2 * (nf.value - 1)
+    return psd[:, :nf.value], np.arange(nf.value) / (L * dt)
 
 
 def fr_set_tile(ctx, epb):
