@@ -54,15 +54,31 @@ def _expand(fv, h, d, dim, Np):
 
 
 class FRSolver:
-    """Residual, RK4 and forces on one mesh for one physics."""
+    """Residual, RK4 and forces on one mesh for one physics.
 
-    def __init__(self, mesh, phys):
+    ``source``: optional list of Gaussian monopoles (A, k, (xs, ys, zs), freq)
+    added to the energy equation (Appendix D, Eq. D.1):
+    s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi freq_m t), evaluated at
+    the solution points at the stage time."""
+
+    def __init__(self, mesh, phys, source=None):
         self.m = mesh
         self.ph = phys
+        self.source = list(source) if source else []
+
+    def source_term(self, t):
+        """s(x_sp, t) [E, Nsp] of Eq. D.1 (zeros without sources)."""
+        x = self.m.xsp
+        s = np.zeros(x.shape[:2])
+        for A, k, xs, freq in self.source:
+            r2 = np.sum((x - np.asarray(xs, float)[None, None, :x.shape[2]]) ** 2, axis=-1)
+            s += A * np.exp(-k * r2) * np.sin(2.0 * np.pi * freq * t)
+        return s
 
     # -------------------------------------------------------------------
-    def residual(self, u, want_faces=False):
-        """R(u) for u [E, nvar, Nsp]; optionally also face data for forces."""
+    def residual(self, u, want_faces=False, t=0.0):
+        """R(u) for u [E, nvar, Nsp] at time t (the time enters only through
+        the source term); optionally also face data for forces."""
         m, ph = self.m, self.ph
         ref = m.ref
         E, dim, Np, Nfp, nf = m.E, m.dim, m.Np, m.Nfp, m.nface
@@ -171,18 +187,21 @@ class FRSolver:
                 FDn = nsg * _contract(Ftd, lv, d, dim).reshape(E, nv, Nfp)
                 div += _expand(Fc[:, f] - FDn, h, d, dim, Np)
         R = -div.reshape(E, nv, -1) / J[:, None]
+        if self.source:
+            R[:, nv - 1, :] += self.source_term(t)
         if not want_faces:
             return R
         return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc}
 
     # -------------------------------------------------------------------
-    def rk4_step(self, u, dt):
-        """Classic RK4: k1 = R(u), k2 = R(u + dt/2 k1), k3 = R(u + dt/2 k2),
-        k4 = R(u + dt k3); u + dt (k1 + 2 k2 + 2 k3 + k4)/6."""
-        k1 = self.residual(u)
-        k2 = self.residual(u + 0.5 * dt * k1)
-        k3 = self.residual(u + 0.5 * dt * k2)
-        k4 = self.residual(u + dt * k3)
+    def rk4_step(self, u, dt, t=0.0):
+        """Classic RK4 from time t: k1 = R(u, t), k2 = R(u + dt/2 k1, t + dt/2),
+        k3 = R(u + dt/2 k2, t + dt/2), k4 = R(u + dt k3, t + dt);
+        u + dt (k1 + 2 k2 + 2 k3 + k4)/6."""
+        k1 = self.residual(u, t=t)
+        k2 = self.residual(u + 0.5 * dt * k1, t=t + 0.5 * dt)
+        k3 = self.residual(u + 0.5 * dt * k2, t=t + 0.5 * dt)
+        k4 = self.residual(u + dt * k3, t=t + dt)
         return u + dt * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
 
     # -------------------------------------------------------------------

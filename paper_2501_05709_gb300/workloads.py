@@ -114,13 +114,14 @@ def _structured_conn(ne, periodic, bc_lo, bc_hi):
     return conn
 
 
-def box_mesh(dim, n, lo, hi, q=1, periodic=None, walls_y=False, curve=0.0, seed=0):
+def box_mesh(dim, n, lo, hi, q=1, periodic=None, walls_y=False, curve=0.0, seed=0, bc_tag=None):
     """Uniform box of n^dim (or n[0] x n[1] x n[2]) elements.
 
     curve > 0 displaces every node by a smooth field periodic on the box
     (amplitude ``curve`` times the element size, seeded phases), which makes
     elements curved (q=2) or skewed (q=1) while periodic faces still match.
     walls_y puts BC_WALL on both y faces (direction 1 not periodic).
+    Non-periodic faces carry ``bc_tag`` (default BC_WALL).
     """
     ne = list(n) if np.ndim(n) else [int(n)] * dim
     lo = np.broadcast_to(np.asarray(lo, float), (dim,)).copy()
@@ -153,7 +154,7 @@ def box_mesh(dim, n, lo, hi, q=1, periodic=None, walls_y=False, curve=0.0, seed=
         grid = grid + disp
     shift = np.diag(hi - lo)
     nodes = _elem_nodes_from_grid(grid, q, dim, ne, shift)
-    bc = [BC_WALL] * dim
+    bc = [BC_WALL if bc_tag is None else bc_tag] * dim
     conn = _structured_conn(ne, periodic, bc, bc)
     return nodes, conn
 
