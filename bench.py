@@ -221,6 +221,10 @@ WORKLOADS = {
                    "hexes, span 0.2c, FR p=3 (6,400,000 DOF), Re=23000, M=0.2, AoA 3 deg, 1% seeded noise, "
                    "RK4 dt=1.37e-6 (advective+viscous CFL estimate), wall forces and an 18,840-point FW-H cylinder (r=1.5c) sampled "
                    "every step",
+    "monopole125k_p3": "Appendix D.1 monopole in a quiescent box: [-5,5]^3, 50^3 = 125,000 hexes, FR p=3 "
+                       "(8,000,000 DOF), Euler, characteristic far field, Gaussian energy source A=0.05, k=100, "
+                       "f=0.5 at the centre (Eq. D.1), rho=1, p=1/gamma (c=1), RK4 dt=0.00625, a 1.5-radius FW-H "
+                       "sphere sampled every step",
     "batch12_p3": "12 NACA 4-digit candidates (PCG64 seed 1: m~U[0,0.06], p~U[0.2,0.6], t~U[0.08,0.16], "
                   "20k-80k quadratic hexes each, 599,888 in total, 38.4M DOF) in one context, FR p=3, Re=23000, "
                   "M=0.2, AoA 3 deg, RK4 at each candidate's own stable dt (0.27e-6..2.0e-6), forces and one FW-H "
@@ -245,6 +249,17 @@ def build_workload(name):
         def state(ctx):
             return np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=MACH), 0, 1))
         return [(nodes, conn)], opts, state, [], False, None
+    if name == "monopole125k_p3":
+        nodes, conn, o32, free = C.monopole_box_setup(50, 3, F.FR_FP32)
+        rho, vel, pinf = free
+
+        def opts(prec):
+            return C.monopole_box_setup(50, 3, prec)[2]
+
+        def state(ctx):
+            return W.perturbed_uniform(ctx.nelem, ctx.nsp, rho, vel, pinf, amplitude=0.0)
+        surf = W.sphere_surface(1.5, 30, 2 * np.pi / 45)[0]
+        return [(nodes, conn)], opts, state, [surf], False, None
     if name == "naca100k_p3":
         params = [{"naca": (0.02, 0.4, 0.12), "n_theta": 250, "n_r": 100}]
     elif name == "batch12_p3":
@@ -268,11 +283,16 @@ def build_workload(name):
     return meshes, opts, state, [surf] * len(meshes), True, dts
 
 
+def ctx_viscous(o):
+    return int(o.viscous)
+
+
 def gpu_leg(args, rank, world, local_rank):
     import numpy as np
     import torch
 
     from paper_2501_05709_gb300 import build as B
+    from paper_2501_05709_gb300 import cases as C
     from paper_2501_05709_gb300 import fr as F
     from paper_2501_05709_gb300 import workloads as W
 
@@ -286,6 +306,9 @@ def gpu_leg(args, rank, world, local_rank):
     ctx = F.fr_mesh_load(meshes, opts(prec))
     for k, d in enumerate(dts or []):
         F.fr_set_cand_dt(ctx, k, d)
+    if args.workload.startswith("monopole"):
+        F.fr_set_source(ctx, 0, C.MONOPOLE_SOURCE, 0.0)
+    viscous = bool(ctx_viscous(opts(prec)))
     p = ctx.order
     u0 = state_of(ctx)
     E, nsp = ctx.nelem, ctx.nsp
@@ -333,7 +356,7 @@ def gpu_leg(args, rank, world, local_rank):
     # per-kernel durations of the same steps, events around each launch
     kms, kn = F.fr_profile_step(ctx, args.steps, sh)
     hbm, peak_kind = peaks()
-    ab = algorithmic_bytes(E, p, rsz, curved=curved)
+    ab = algorithmic_bytes(E, p, rsz, viscous=viscous, curved=curved)
     resid_ms = kms[2] / max(kn[2], 1)
     achieved = ab["resid"] / (resid_ms / 1e3) / 1e9
     def kstat(i, key):
@@ -371,6 +394,8 @@ def gpu_leg(args, rank, world, local_rank):
         c64 = F.fr_mesh_load(meshes, opts(F.FR_FP64))
         for k, d in enumerate(dts or []):
             F.fr_set_cand_dt(c64, k, d)
+        if args.workload.startswith("monopole"):
+            F.fr_set_source(c64, 0, C.MONOPOLE_SOURCE, 0.0)
         F.fr_state_set(c64, u0)
         for k, srf in enumerate(surfaces):
             F.fwh_register(c64, k, srf, cap, 1)

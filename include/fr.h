@@ -150,6 +150,24 @@ int fr_rk_step(fr_ctx* ctx, int nsteps, void* stream);
  * Errors: FR_EINVAL (cand out of range, dt <= 0), FR_ENOMEM. */
 int fr_set_cand_dt(fr_ctx* ctx, int cand, double dt);
 
+/* Energy source of Appendix D (Eq. D.1 and its multi-monopole form): adds
+ *   s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi f_m t)
+ * to the energy equation of candidate `cand`, evaluated at every solution
+ * point at the stage time (classic RK4: t_n, t_n + dt/2, t_n + dt/2,
+ * t_n + dt; fr_residual uses t_n).
+ *   src   host, [nsrc][6] doubles (A, k, x, y, z, f) per source, copied;
+ *         0 <= nsrc <= 4 (nsrc = 0 removes the candidate's sources); k >= 0;
+ *         z ignored in 2D.  Elements whose weights exp(-k|x - x_m|^2) are all
+ *         below 1e-30 are skipped.
+ *   t0    the candidate's time t_n from now on; every RK4 step advances it by
+ *         the candidate's dt (fr_set_cand_dt or the options' dt).
+ * Errors: FR_EINVAL (bad candidate, nsrc, non-finite values, k < 0),
+ * FR_ENOMEM.  Rebuilds the step's CUDA graph on its next replay. */
+int fr_set_source(fr_ctx* ctx, int cand, int nsrc, const double* src, double t0);
+
+/* The candidate's source time t_n (0 if no source was ever set). */
+int fr_source_time(const fr_ctx* ctx, int cand, double* t);
+
 /* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
  * use for the current surfaces and options).  Bit-identical results. */
 int fr_rk_step_graph(fr_ctx* ctx, int nsteps, void* stream);

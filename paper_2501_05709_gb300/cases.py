@@ -195,10 +195,81 @@ def precision_study(steps=25000, dt=4e-5, sample_every=4, n_theta=60, n_r=20, n_
     return out
 
 
+# ---------------------------------------------------------------- Appendix D.1: monopole in a box
+MONOPOLE_SOURCE = [(0.05, 100.0, (0.0, 0.0, 0.0), 0.5)]   # A, k, position, frequency (Eq. D.1)
+
+
+def monopole_box_setup(n=50, order=3, precision=F.FR_FP32, half=5.0, cfl=0.5):
+    """Quiescent Euler box [-half, half]^3 of n^3 hexes with characteristic
+    far-field faces (the paper's Riemann-invariant boundaries), free stream at
+    rest with rho = 1, p = 1/gamma (c = 1), and the explicit step
+    cfl * h / ((p+1)^2 c) (RK4 with this FR discretisation: 0.6 stays stable
+    on the quiescent box, 0.8 does not; 0.5 is used).  Returns (nodes, conn,
+    options, free stream)."""
+    nodes, conn = W.box_mesh(3, n, -half, half, q=1, periodic=[False] * 3, bc_tag=W.BC_FARFIELD)
+    rho, vel, p = 1.0, np.zeros(3), 1.0 / GAMMA
+    dt = cfl * (2.0 * half / n) / ((order + 1) ** 2 * 1.0)
+    opts = F.options(order=order, precision=precision, viscous=False, rho_inf=rho, p_inf=p, vel_inf=(0.0, 0.0, 0.0),
+                     dt=dt)
+    return nodes, conn, opts, (rho, vel, p)
+
+
+def run_monopole_box(order=3, n=50, t_end=8.0, precision=F.FR_FP32, observer=(0.0, 3.0, 0.0), radius=1.5,
+                     graph=True):
+    """Appendix D.1: a monopole (Eq. D.1) at the centre of a quiescent box;
+    the acoustic pressure at the observer directly from the flow solution and
+    from the FW-H integral over a sphere of the given radius (sampled every
+    step).  Returns the two series on the FW-H observer times and their
+    relative RMS difference."""
+    import torch
+    nodes, conn, opts, free = monopole_box_setup(n, order, precision)
+    rho, vel, p = free
+    surf = W.sphere_surface(radius, 30, 2 * np.pi / 45)
+    steps = int(math.ceil(t_end / opts.dt))
+    out = {"order": order, "elements": len(nodes), "steps": steps, "dt": opts.dt}
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        F.fr_state_set(ctx, W.perturbed_uniform(ctx.nelem, ctx.nsp, rho, vel, p, amplitude=0.0))
+        F.fr_set_source(ctx, 0, MONOPOLE_SOURCE, 0.0)
+        hs = F.fwh_register(ctx, 0, surf[0], steps, 1)
+        ho = F.fwh_register(ctx, 0, np.asarray(observer, float)[None], steps, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (F.fr_rk_step_graph if graph else F.fr_rk_step)(ctx, steps)
+        torch.cuda.synchronize()
+        out["seconds"] = time.perf_counter() - t0
+        out["dof_stages_per_s"] = ctx.nelem * ctx.nsp * 4 * steps / out["seconds"]
+        hist = F.fwh_history(ctx, hs, len(surf[0]))            # totals (rho, V, p)
+        direct = F.fwh_history(ctx, ho, 1)[:, 0, 4] - p         # p' at the observer
+    # sampling happens at the start of each step: record k is the state at t = k dt
+    c0 = math.sqrt(GAMMA * p / rho)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    pout, nt, t0w = F.fwh_integrate(dev(hist), dev(surf[0]), dev(surf[1]), dev(surf[2]), opts.dt, 0.0,
+                                    np.asarray(observer, float)[None], [0.0, 0.0, 0.0], c0, rho, p)
+    hyb = pout[0, :nt[0]].cpu().numpy()
+    ts = t0w[0] + opts.dt * np.arange(nt[0])
+    # compare where both exist: the FW-H window runs past the last flow sample
+    # by the largest surface-to-observer delay
+    keep = ts <= opts.dt * (len(direct) - 1)
+    ts, hyb = ts[keep], hyb[keep]
+    dirp = np.interp(ts, opts.dt * np.arange(len(direct)), direct)
+    rms = lambda a: float(np.sqrt(np.mean(a ** 2)))
+    out.update(times=ts, direct=dirp, hybrid=hyb, window=int(keep.sum()),
+               rel_rms_diff=rms(hyb - dirp) / rms(dirp),
+               rel_rms_diff_mean_removed=rms((hyb - hyb.mean()) - (dirp - dirp.mean())) / rms(dirp - dirp.mean()),
+               direct_rms=rms(dirp), hybrid_rms=rms(hyb))
+    return out
+
+
 if __name__ == "__main__":
     import json
     import sys
     if len(sys.argv) > 1 and sys.argv[1] == "naca-precision":
         print(json.dumps(precision_study(), default=float))
+    elif len(sys.argv) > 1 and sys.argv[1] == "monopole-box":
+        res = {}
+        for order in (1, 2, 3):
+            r = run_monopole_box(order=order, t_end=12.0)
+            res[f"p{order}"] = {k: v for k, v in r.items() if not isinstance(v, np.ndarray)}
+        print(json.dumps(res, default=float))
     else:
-        print("usage: python -m paper_2501_05709_gb300.cases naca-precision")
+        print("usage: python -m paper_2501_05709_gb300.cases naca-precision|monopole-box")

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,9 +80,36 @@ struct fr_ctx {
     int device = 0;
     double* stage64 = nullptr;  // double staging buffer for FP32 state transfers
     void* dte = nullptr;        // per-element time step (Real[E]) once a candidate sets its own
+    std::vector<double> cand_dt;  // per-candidate step (host copy)
+    // energy sources (Appendix D, Eq. D.1), see frk::Src
+    std::vector<std::vector<std::array<double, 6>>> srcs;  // per candidate: A, k, x, y, z, f
+    int32_t* src_entry = nullptr;  // device [E]; null: no sources anywhere
+    int32_t* src_cand = nullptr;   // device [entries]
+    void* src_w = nullptr;         // device Real [entries][MAXSRC][nsp]
+    double *src_A = nullptr, *src_f = nullptr;  // device [ncand][MAXSRC]
+    double* tnow = nullptr;        // device [ncand]: time at the start of the next step
+    double* dtc = nullptr;         // device [ncand]: step of each candidate
 };
 
 namespace {
+
+template <typename Real>
+frk::Src<Real> src_of(const fr_ctx* c, double cfac) {
+    frk::Src<Real> r;
+    if (!c->src_entry) return r;
+    r.entry = c->src_entry;
+    r.cand = c->src_cand;
+    r.w = static_cast<const Real*>(c->src_w);
+    r.A = c->src_A;
+    r.f = c->src_f;
+    r.tnow = c->tnow;
+    r.cfac = cfac;
+    return r;
+}
+
+__global__ void k_time_advance(double* __restrict__ tnow, const double* __restrict__ dtc, int ncand) {
+    for (int c = threadIdx.x; c < ncand; c += blockDim.x) tnow[c] += dtc[c];
+}
 
 template <typename Real>
 frk::Geo<Real> geo_of(const fr_ctx* c) {
@@ -273,10 +301,16 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         st.us = us;
         st.acc = acc;
         st.uf_next = uf_out;
+        st.src = src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5);
         if (pr) pr->mark_begin(2);
         rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
+    }
+    if (c->src_entry) {
+        k_time_advance<<<1, 32, 0, s>>>(c->tnow, c->dtc, c->ncand);
+        ++c->launches;
+        CK(cudaGetLastError());
     }
     return FR_OK;
 }
@@ -299,6 +333,7 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     st.dte = nullptr;
     st.R = R;
     st.u0 = st.us = st.acc = st.uf_next = nullptr;
+    st.src = src_of<Real>(c, 0.0);
     rc = L_resid<Real>(c, u, uf, st, s);
     CKL(rc, "residual kernel");
     return FR_OK;
@@ -362,7 +397,7 @@ void release(fr_ctx* c) {
     if (!c) return;
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
-                    c->fpart};
+                    c->fpart, c->src_entry, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -671,6 +706,8 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         return fail(FR_ECUDA, "cannot create a stream");
     }
     default_launch(c);
+    c->cand_dt.assign(ncand, o->dt);
+    c->srcs.assign(ncand, {});
     {
         // first use of each kernel: shared-memory opt-in outside any capture
         const int64_t keepE = c->E;
@@ -874,6 +911,8 @@ __global__ void k_fill_f(float* a, int64_t n, float v) {
 extern "C" int fr_set_cand_dt(fr_ctx* c, int cand, double dt) {
     if (!c || cand < 0 || cand >= c->ncand || !(dt > 0.0)) return fail(FR_EINVAL, "bad candidate or dt");
     CK(cudaDeviceSynchronize());
+    c->cand_dt[cand] = dt;
+    if (c->dtc) CK(cudaMemcpy(c->dtc + cand, &dt, sizeof(double), cudaMemcpyHostToDevice));
     if (!c->dte) {
         if (cudaMalloc(&c->dte, size_t(c->E) * c->rsz) != cudaSuccess) {
             c->dte = nullptr;
@@ -891,6 +930,119 @@ extern "C" int fr_set_cand_dt(fr_ctx* c, int cand, double dt) {
     c->launches += 1;
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
+    return FR_OK;
+}
+
+// ---------------------------------------------------------------- energy sources (Appendix D)
+namespace {
+
+template <typename Real>
+int upload_src_weights(fr_ctx* c, const std::vector<double>& w) {
+    std::vector<Real> h(w.begin(), w.end());
+    if (cudaMalloc(&c->src_w, sizeof(Real) * std::max<size_t>(1, h.size())) != cudaSuccess) return FR_ENOMEM;
+    if (!h.empty() && cudaMemcpy(c->src_w, h.data(), sizeof(Real) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FR_ECUDA;
+    return FR_OK;
+}
+
+// Rebuilds the device source table from c->srcs: every element with a
+// solution point where some exp(-k_m |x - x_m|^2) exceeds 1e-30 gets an entry.
+int rebuild_sources(fr_ctx* c) {
+    for (void** b : {reinterpret_cast<void**>(&c->src_entry), reinterpret_cast<void**>(&c->src_cand), &c->src_w}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    bool any = false;
+    for (const auto& v : c->srcs) any = any || !v.empty();
+    if (!any) return FR_OK;
+    const int dim = c->dim, nsp = c->nsp, nf = c->nf, nfp = c->nfp, M = frk::MAXSRC;
+    std::vector<int32_t> entry(size_t(c->E), -1), cand_of;
+    std::vector<double> w;
+    std::vector<double> xyz(size_t(nsp) * dim), J(nsp), S(size_t(dim) * dim * nsp), N(size_t(nf) * nfp * dim);
+    for (int k = 0; k < c->ncand; ++k) {
+        const auto& sv = c->srcs[k];
+        if (sv.empty()) continue;
+        const int nq = c->q[k] + 1;
+        const int nn = dim == 2 ? nq * nq : nq * nq * nq;
+        for (int64_t e = c->cand_off[k]; e < c->cand_off[k + 1]; ++e) {
+            frg::element_geometry(dim, c->q[k], c->ref, c->nodes[k].data() + (e - c->cand_off[k]) * nn * dim,
+                                  xyz.data(), J.data(), S.data(), N.data());
+            std::vector<double> we(size_t(M) * nsp, 0.0);
+            bool active = false;
+            for (size_t m = 0; m < sv.size(); ++m)
+                for (int sp = 0; sp < nsp; ++sp) {
+                    double r2 = 0.0;
+                    for (int i = 0; i < dim; ++i) {
+                        const double d = xyz[size_t(sp) * dim + i] - sv[m][2 + i];
+                        r2 += d * d;
+                    }
+                    const double v = std::exp(-sv[m][1] * r2);
+                    we[m * nsp + sp] = v;
+                    if (v > 1e-30) active = true;
+                }
+            if (!active) continue;
+            entry[e] = int32_t(cand_of.size());
+            cand_of.push_back(k);
+            w.insert(w.end(), we.begin(), we.end());
+        }
+    }
+    std::vector<double> A(size_t(c->ncand) * M, 0.0), f(size_t(c->ncand) * M, 0.0);
+    for (int k = 0; k < c->ncand; ++k)
+        for (size_t m = 0; m < c->srcs[k].size(); ++m) {
+            A[size_t(k) * M + m] = c->srcs[k][m][0];
+            f[size_t(k) * M + m] = c->srcs[k][m][5];
+        }
+    int rc;
+    if ((rc = upload(reinterpret_cast<void**>(&c->src_entry), entry)) ||
+        (rc = upload(reinterpret_cast<void**>(&c->src_cand), cand_of.empty() ? std::vector<int32_t>{0} : cand_of)))
+        return rc;
+    rc = c->prec == FR_FP64 ? upload_src_weights<double>(c, w) : upload_src_weights<float>(c, w);
+    if (rc) return rc;
+    if (cudaMemcpy(c->src_A, A.data(), A.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->src_f, f.data(), f.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FR_ECUDA;
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, double t0) {
+    if (!c || cand < 0 || cand >= c->ncand || nsrc < 0 || nsrc > frk::MAXSRC || (nsrc > 0 && !src) ||
+        !std::isfinite(t0))
+        return fail(FR_EINVAL, "bad argument (0 <= nsrc <= 4 sources of 6 values each)");
+    std::vector<std::array<double, 6>> sv(nsrc);
+    for (int m = 0; m < nsrc; ++m)
+        for (int i = 0; i < 6; ++i) {
+            sv[m][i] = src[m * 6 + i];
+            if (!std::isfinite(sv[m][i])) return fail(FR_EINVAL, "non-finite source parameter");
+        }
+    for (const auto& v : sv)
+        if (!(v[1] >= 0.0)) return fail(FR_EINVAL, "source range factor k must be >= 0");
+    CK(cudaDeviceSynchronize());
+    if (!c->tnow) {
+        const size_t nc = size_t(c->ncand);
+        if (cudaMalloc(&c->tnow, nc * 8) != cudaSuccess || cudaMalloc(&c->dtc, nc * 8) != cudaSuccess ||
+            cudaMalloc(&c->src_A, nc * frk::MAXSRC * 8) != cudaSuccess ||
+            cudaMalloc(&c->src_f, nc * frk::MAXSRC * 8) != cudaSuccess)
+            return fail(FR_ENOMEM, "cannot allocate source tables");
+        CK(cudaMemset(c->tnow, 0, nc * 8));
+        CK(cudaMemcpy(c->dtc, c->cand_dt.data(), nc * 8, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(c->tnow + cand, &t0, 8, cudaMemcpyHostToDevice));
+    c->srcs[cand] = sv;
+    const int rc = rebuild_sources(c);
+    if (rc) return fail(rc, "cannot build the source table");
+    invalidate_graph(c);
+    CK(cudaDeviceSynchronize());
+    return FR_OK;
+}
+
+extern "C" int fr_source_time(const fr_ctx* c, int cand, double* t) {
+    if (!c || !t || cand < 0 || cand >= c->ncand) return fail(FR_EINVAL, "bad argument");
+    *t = 0.0;
+    if (!c->tnow) return FR_OK;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(t, c->tnow + cand, 8, cudaMemcpyDeviceToHost));
     return FR_OK;
 }
 

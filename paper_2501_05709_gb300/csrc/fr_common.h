@@ -62,6 +62,24 @@ struct Geo {
 //   stage 4: input us;  u0 = u0 + acc + dt/6 k4
 // uf_next (stages 1-4): traces of the stage's output state, for the next stage.
 // dte (optional): per-element time step overriding dt.
+// src (optional, entry == nullptr: none): energy source of Appendix D, Eq. D.1,
+//   s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi f_m t), added to the
+//   energy residual of the elements that carry one, at the stage time
+//   t = tnow[cand] + cfac * dt (cfac = 0, 1/2, 1/2, 1 for stages 1-4; 0 for
+//   stage 0).  entry[e] indexes the element's weights
+//   w[entry][m][sp] = exp(-k_m |x_sp - x_m|^2) (-1: none); A, f are per
+//   candidate [cand][MAXSRC] (unused slots A = 0).
+constexpr int MAXSRC = 4;
+template <typename Real>
+struct Src {
+    const int32_t* entry = nullptr;
+    const int32_t* cand = nullptr;
+    const Real* w = nullptr;
+    const double* A = nullptr;
+    const double* f = nullptr;
+    const double* tnow = nullptr;
+    double cfac = 0.0;
+};
 template <typename Real>
 struct Stage {
     int stage;
@@ -72,6 +90,7 @@ struct Stage {
     Real* us;
     Real* acc;
     Real* uf_next;
+    Src<Real> src{};
 };
 
 // One warp per element; epb elements (warps) per block.

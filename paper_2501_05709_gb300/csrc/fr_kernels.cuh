@@ -1034,6 +1034,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     // F: residual and RK stage per solution point; the new stage state
     // replaces su for the traces
     const Real dt = st.dte ? st.dte[e] : st.dt;
+    const int sx = st.src.entry ? st.src.entry[e] : -1;   // energy source entry (Eq. D.1), or none
 #pragma unroll
     for (int s = 0; s < NSPW; ++s) {
         const int sp = lane + 32 * s;
@@ -1042,7 +1043,18 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const int k = VL::pt(v, sp);
-            const Real r = -sd[k] * iJ;
+            Real r = -sd[k] * iJ;
+            if (v == NV - 1 && sx >= 0) {
+                const int c = st.src.cand[sx];
+                const double t = st.src.tnow[c] + st.src.cfac * double(dt);
+#pragma unroll 1
+                for (int m = 0; m < MAXSRC; ++m) {
+                    const double a = st.src.A[c * MAXSRC + m];
+                    if (a != 0.0)
+                        r += Real(a * sinpi(2.0 * st.src.f[c * MAXSRC + m] * t)) *
+                             st.src.w[(int64_t(sx) * MAXSRC + m) * NSP + sp];
+                }
+            }
             const int64_t gi = base + v * NSP + sp;
             Real u0v = Real(0), accv = Real(0);
             if (st.stage >= 2) {

@@ -85,6 +85,8 @@ _SIGS = {
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
     "fwh_psd": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_int,
                           C.POINTER(C.c_int), C.c_void_p]),
+    "fr_set_source": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double]),
+    "fr_source_time": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "fr_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
@@ -331,6 +333,21 @@ def fwh_psd(p, dt, nseg=3, nt=None, psd=None, stream=None):
                          _stream(stream)))
     L = 2 * (nf.value - 1)
     return psd[:, :nf.value], np.arange(nf.value) / (L * dt)
+
+
+def fr_set_source(ctx, cand, sources, t0=0.0):
+    """Energy sources of Eq. D.1 for candidate cand: sources = [(A, k, (x, y, z), f), ...]
+    (at most 4); the candidate's time becomes t0."""
+    arr = np.ascontiguousarray([[A, k, *list(xs)[:3], *([0.0] * (3 - len(xs))), f] for A, k, xs, f in sources],
+                               dtype=np.float64).reshape(-1, 6)
+    _check(lib().fr_set_source(ctx.handle, int(cand), int(arr.shape[0]), _ptr(arr) if arr.size else None,
+                               float(t0)))
+
+
+def fr_source_time(ctx, cand=0):
+    t = C.c_double()
+    _check(lib().fr_source_time(ctx.handle, int(cand), C.byref(t)))
+    return t.value
 
 
 def fr_set_tile(ctx, epb):
