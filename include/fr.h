@@ -168,6 +168,24 @@ int fr_set_source(fr_ctx* ctx, int cand, int nsrc, const double* src, double t0)
 /* The candidate's source time t_n (0 if no source was ever set). */
 int fr_source_time(const fr_ctx* ctx, int cand, double* t);
 
+/* Adaptive time step (Section 3.1 runs with adaptive time stepping; its
+ * integrator's coefficients are in the cited work, not in the paper, so the
+ * update stays classic RK4 and only the step size adapts).  With cfl > 0,
+ * every RK4 step first sets each candidate's step from the state at the start
+ * of the step:
+ *   dt = cfl / max_e lambda_e,
+ *   lambda_e = max_sp (|V| + c) (p+1)^2 / h_e + max_sp (mu / rho) (p+1)^4 / h_e^2
+ * (the viscous term only with viscous physics), h_e = min over solution
+ * points and directions d of 2 |J| / |S[d,:]|.  All on the device, so graph
+ * replay adapts too.  cfl <= 0 returns to the fixed steps (fr_set_cand_dt or
+ * the options' dt).  Forces keep per-step averages; surface samples are taken
+ * every `every` steps whatever their spacing in time.
+ * Errors: FR_EINVAL (non-finite cfl), FR_ENOMEM. */
+int fr_set_adaptive_dt(fr_ctx* ctx, double cfl);
+
+/* The candidate's current step (the last adaptive one, or the fixed one). */
+int fr_cand_dt(const fr_ctx* ctx, int cand, double* dt);
+
 /* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
  * use for the current surfaces and options).  Bit-identical results. */
 int fr_rk_step_graph(fr_ctx* ctx, int nsteps, void* stream);

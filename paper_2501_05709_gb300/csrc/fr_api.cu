@@ -89,6 +89,11 @@ struct fr_ctx {
     double *src_A = nullptr, *src_f = nullptr;  // device [ncand][MAXSRC]
     double* tnow = nullptr;        // device [ncand]: time at the start of the next step
     double* dtc = nullptr;         // device [ncand]: step of each candidate
+    // adaptive time step (cfl > 0: on)
+    double adaptive_cfl = 0.0;
+    void* hlen = nullptr;                // device Real [E]: element length
+    int64_t* cand_off_d = nullptr;       // device [ncand + 1]
+    unsigned long long* lam = nullptr;   // device [ncand]: max spectral rate (double bits)
 };
 
 namespace {
@@ -110,6 +115,21 @@ frk::Src<Real> src_of(const fr_ctx* c, double cfac) {
 __global__ void k_time_advance(double* __restrict__ tnow, const double* __restrict__ dtc, int ncand) {
     for (int c = threadIdx.x; c < ncand; c += blockDim.x) tnow[c] += dtc[c];
 }
+
+// adaptive step of each candidate, dt = cfl / lambda_max, into the per-element
+// step and the per-candidate step
+template <typename Real>
+__global__ void k_dt_fill(const unsigned long long* __restrict__ lam, double cfl, const int64_t* __restrict__ cand_off,
+                          int ncand, int64_t E, Real* __restrict__ dte, double* __restrict__ dtc) {
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += int64_t(gridDim.x) * blockDim.x) {
+        int c = 0;
+        while (c + 1 < ncand && e >= cand_off[c + 1]) ++c;
+        const double dt = cfl / __longlong_as_double(static_cast<long long>(lam[c]));
+        dte[e] = Real(dt);
+        if (e == cand_off[c]) dtc[c] = dt;
+    }
+}
+
 
 template <typename Real>
 frk::Geo<Real> geo_of(const fr_ctx* c) {
@@ -267,10 +287,30 @@ int ensure_traces(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
 // residual kernel writes the traces of its output into ufb[s&1], so the step
 // ends with the traces of the new u0 in ufb[0].
 template <typename Real>
+int enqueue_adaptive_dt(fr_ctx* c, cudaStream_t s) {
+    CK(cudaMemsetAsync(c->lam, 0, sizeof(unsigned long long) * c->ncand, s));
+    const auto ph = phys_of<Real>(c);
+    const Real* u = static_cast<const Real*>(c->u0);
+    const Real* h = static_cast<const Real*>(c->hlen);
+    int rc = c->dim == 2 ? frl::cfl<Real, 2>(c->p, u, h, c->E, c->cand_off_d, c->ncand, ph, c->lam, s)
+                         : frl::cfl<Real, 3>(c->p, u, h, c->E, c->cand_off_d, c->ncand, ph, c->lam, s);
+    CKL(rc, "time step kernel");
+    k_dt_fill<Real><<<256, 256, 0, s>>>(c->lam, c->adaptive_cfl, c->cand_off_d, c->ncand, c->E,
+                                        static_cast<Real*>(c->dte), c->dtc);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    return FR_OK;
+}
+
+template <typename Real>
 int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
     Real* u0 = static_cast<Real*>(c->u0);
     Real* us = static_cast<Real*>(c->us);
     Real* acc = static_cast<Real*>(c->acc);
+    if (c->adaptive_cfl > 0.0) {
+        const int rc = enqueue_adaptive_dt<Real>(c, s);
+        if (rc) return rc;
+    }
     for (int stage = 1; stage <= 4; ++stage) {
         const Real* in = (stage == 1) ? u0 : us;
         const Real* uf_in = static_cast<const Real*>(c->ufb[(stage - 1) & 1]);
@@ -397,7 +437,8 @@ void release(fr_ctx* c) {
     if (!c) return;
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
-                    c->fpart, c->src_entry, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc};
+                    c->fpart, c->src_entry, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc,
+                    c->hlen, c->cand_off_d, c->lam};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -614,7 +655,25 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         }
     }
     c->affine = affine ? 1 : 0;
+    // element length of the adaptive time step: min over points and
+    // directions of 2 |J| / |S[d,:]|
+    std::vector<double> hl(size_t(E), 1e300);
+    for (int64_t e = 0; e < E; ++e)
+        for (int d = 0; d < dim; ++d)
+            for (int sp = 0; sp < nsp; ++sp) {
+                double n2 = 0.0;
+                for (int i = 0; i < dim; ++i) {
+                    const double v = Sh[(e * dim * dim + d * dim + i) * nsp + sp];
+                    n2 += v * v;
+                }
+                hl[e] = std::min(hl[e], 2.0 * Jh[e * nsp + sp] / std::sqrt(n2));
+            }
     int rc;
+    if ((rc = upload_real(&c->hlen, hl, c->prec)) ||
+        (rc = upload(reinterpret_cast<void**>(&c->cand_off_d), c->cand_off))) {
+        release(c);
+        return rc;
+    }
     if (affine) {
         std::vector<double> S1(E * dim * dim), J1(E), N1(E * nf * dim);
         for (int64_t e = 0; e < E; ++e) {
@@ -1021,11 +1080,15 @@ extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, d
     CK(cudaDeviceSynchronize());
     if (!c->tnow) {
         const size_t nc = size_t(c->ncand);
-        if (cudaMalloc(&c->tnow, nc * 8) != cudaSuccess || cudaMalloc(&c->dtc, nc * 8) != cudaSuccess ||
+        if (cudaMalloc(&c->tnow, nc * 8) != cudaSuccess ||
             cudaMalloc(&c->src_A, nc * frk::MAXSRC * 8) != cudaSuccess ||
             cudaMalloc(&c->src_f, nc * frk::MAXSRC * 8) != cudaSuccess)
             return fail(FR_ENOMEM, "cannot allocate source tables");
         CK(cudaMemset(c->tnow, 0, nc * 8));
+    }
+    if (!c->dtc) {
+        const size_t nc = size_t(c->ncand);
+        if (cudaMalloc(&c->dtc, nc * 8) != cudaSuccess) return fail(FR_ENOMEM, "cannot allocate source tables");
         CK(cudaMemcpy(c->dtc, c->cand_dt.data(), nc * 8, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(c->tnow + cand, &t0, 8, cudaMemcpyHostToDevice));
@@ -1034,6 +1097,64 @@ extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, d
     if (rc) return fail(rc, "cannot build the source table");
     invalidate_graph(c);
     CK(cudaDeviceSynchronize());
+    return FR_OK;
+}
+
+// per-element and per-candidate step buffers (filled with the current steps)
+int ensure_dt_buffers(fr_ctx* c) {
+    const size_t nc = size_t(c->ncand);
+    if (!c->dtc) {
+        if (cudaMalloc(&c->dtc, nc * 8) != cudaSuccess) return fail(FR_ENOMEM, "cannot allocate step buffers");
+        CK(cudaMemcpy(c->dtc, c->cand_dt.data(), nc * 8, cudaMemcpyHostToDevice));
+    }
+    if (!c->dte) {
+        if (cudaMalloc(&c->dte, size_t(c->E) * c->rsz) != cudaSuccess) {
+            c->dte = nullptr;
+            return fail(FR_ENOMEM, "cannot allocate per-element time steps");
+        }
+        for (int k = 0; k < c->ncand; ++k) {
+            const int64_t a0 = c->cand_off[k], n = c->cand_off[k + 1] - a0;
+            if (c->prec == FR_FP64) k_fill_d<<<256, 256>>>(static_cast<double*>(c->dte) + a0, n, c->cand_dt[k]);
+            else k_fill_f<<<256, 256>>>(static_cast<float*>(c->dte) + a0, n, float(c->cand_dt[k]));
+            c->launches += 1;
+        }
+        CK(cudaGetLastError());
+    }
+    if (!c->lam && cudaMalloc(&c->lam, nc * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(FR_ENOMEM, "cannot allocate step buffers");
+    return FR_OK;
+}
+
+extern "C" int fr_set_adaptive_dt(fr_ctx* c, double cfl) {
+    if (!c || !std::isfinite(cfl)) return fail(FR_EINVAL, "bad argument");
+    CK(cudaDeviceSynchronize());
+    if (cfl > 0.0) {
+        const int rc = ensure_dt_buffers(c);
+        if (rc) return rc;
+    } else if (c->adaptive_cfl > 0.0) {
+        // back to the fixed steps of fr_set_cand_dt / the options
+        for (int k = 0; k < c->ncand; ++k) {
+            const int64_t a0 = c->cand_off[k], n = c->cand_off[k + 1] - a0;
+            if (c->prec == FR_FP64) k_fill_d<<<256, 256>>>(static_cast<double*>(c->dte) + a0, n, c->cand_dt[k]);
+            else k_fill_f<<<256, 256>>>(static_cast<float*>(c->dte) + a0, n, float(c->cand_dt[k]));
+            c->launches += 1;
+        }
+        CK(cudaMemcpy(c->dtc, c->cand_dt.data(), size_t(c->ncand) * 8, cudaMemcpyHostToDevice));
+    }
+    c->adaptive_cfl = cfl > 0.0 ? cfl : 0.0;
+    invalidate_graph(c);
+    CK(cudaDeviceSynchronize());
+    return FR_OK;
+}
+
+extern "C" int fr_cand_dt(const fr_ctx* c, int cand, double* dt) {
+    if (!c || !dt || cand < 0 || cand >= c->ncand) return fail(FR_EINVAL, "bad argument");
+    if (!c->dtc) {
+        *dt = c->cand_dt[cand];
+        return FR_OK;
+    }
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dt, c->dtc + cand, 8, cudaMemcpyDeviceToHost));
     return FR_OK;
 }
 

@@ -135,6 +135,12 @@ template <typename Real, int DIM>
 int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,
               const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
 
+// per-candidate maximum spectral rate of the adaptive time step (lam holds
+// the bits of non-negative doubles, zeroed by the caller)
+template <typename Real, int DIM>
+int cfl(int P, const Real* u, const Real* hlen, int64_t E, const int64_t* cand_off, int ncand,
+        const frk::Phys<Real>& ph, unsigned long long* lam, void* stream);
+
 // dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual);
 // curved meshes stage per-point metrics and need more
 template <typename Real, int DIM>

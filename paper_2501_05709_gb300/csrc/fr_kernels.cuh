@@ -1101,6 +1101,51 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     }
 }
 
+// Adaptive time step (Section 3.1: adaptive time stepping): per element
+// lambda_e = max_sp (|V| + c) (p+1)^2 / h_e + max_sp (mu / rho) (p+1)^4 / h_e^2
+// in double, h_e the element length (min over points and directions of
+// 2 |J| / |S[d,:]|, precomputed); the candidate's maximum is kept by an
+// atomic maximum on the bits of the non-negative double (order-independent).
+template <int DIM, int P, typename Real>
+__global__ void k_cfl(const Real* __restrict__ u, const Real* __restrict__ hlen, int64_t E,
+                      const int64_t* __restrict__ cand_off, int ncand, const __grid_constant__ Phys<Real> ph,
+                      unsigned long long* __restrict__ lam) {
+    using Z = Sz<DIM, P>;
+    constexpr int NSP = Z::NSP, NV = Z::NV;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    if (e >= E) return;
+    const Real* ue = u + e * NV * NSP;
+    double vmax = 0.0, numax = 0.0;
+    for (int sp = lane; sp < NSP; sp += 32) {
+        const double rho = double(ue[sp]);
+        double m2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            const double m = double(ue[(1 + i) * NSP + sp]);
+            m2 += m * m;
+        }
+        const double p = double(ph.gm1) * (double(ue[(NV - 1) * NSP + sp]) - 0.5 * m2 / rho);
+        const double v = sqrt(m2) / rho + sqrt(double(ph.gamma) * p / rho);
+        vmax = fmax(vmax, v);
+        numax = fmax(numax, double(ph.mu) / rho);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        numax = fmax(numax, __shfl_xor_sync(0xffffffffu, numax, o));
+    }
+    if (lane == 0) {
+        int c = 0;
+        while (c + 1 < ncand && e >= cand_off[c + 1]) ++c;
+        const double h = double(hlen[e]);
+        const double k = double((P + 1) * (P + 1));
+        double l = vmax * k / h;
+        if (ph.viscous) l += numax * k * k / (h * h);
+        atomicMax(lam + c, static_cast<unsigned long long>(__double_as_longlong(l)));
+    }
+}
+
 // Wall force (Section 3.2): FORCE_BLOCKS blocks per candidate each sum, over
 // a slice of that candidate's wall face points, w_fp (p N - tau.N) with N the
 // element's outward area-weighted normal (into the body), p from the interior

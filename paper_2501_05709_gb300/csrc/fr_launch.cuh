@@ -158,6 +158,18 @@ int integrals<FR_REAL, FR_DIM>(int P, const FR_REAL* u, int64_t e_first, int64_t
 #undef C
 }
 
+template <>
+int cfl<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* hlen, int64_t E, const int64_t* cand_off,
+                         int ncand, const frk::Phys<FR_REAL>& ph, unsigned long long* lam, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (E == 0) return 0;
+    const unsigned blocks = unsigned((E + 7) / 8);
+#define C(PP) (frk::k_cfl<FR_DIM, PP, FR_REAL><<<blocks, 256, 0, s>>>(u, hlen, E, cand_off, ncand, ph, lam), \
+               int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
 #undef FR_DISPATCH
 
 }  // namespace frl

@@ -87,6 +87,8 @@ _SIGS = {
                           C.POINTER(C.c_int), C.c_void_p]),
     "fr_set_source": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double]),
     "fr_source_time": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "fr_set_adaptive_dt": (C.c_int, [C.c_void_p, C.c_double]),
+    "fr_cand_dt": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "fr_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
@@ -347,6 +349,17 @@ def fr_set_source(ctx, cand, sources, t0=0.0):
 def fr_source_time(ctx, cand=0):
     t = C.c_double()
     _check(lib().fr_source_time(ctx.handle, int(cand), C.byref(t)))
+    return t.value
+
+
+def fr_set_adaptive_dt(ctx, cfl):
+    """Adaptive RK4 step, dt = cfl / max spectral rate per candidate (cfl <= 0: fixed steps)."""
+    _check(lib().fr_set_adaptive_dt(ctx.handle, float(cfl)))
+
+
+def fr_cand_dt(ctx, cand=0):
+    t = C.c_double()
+    _check(lib().fr_cand_dt(ctx.handle, int(cand), C.byref(t)))
     return t.value
 
 
