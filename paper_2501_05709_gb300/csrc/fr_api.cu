@@ -83,7 +83,8 @@ struct fr_ctx {
     std::vector<double> cand_dt;  // per-candidate step (host copy)
     // energy sources (Appendix D, Eq. D.1), see frk::Src
     std::vector<std::vector<std::array<double, 6>>> srcs;  // per candidate: A, k, x, y, z, f
-    int32_t* src_entry = nullptr;  // device [E]; null: no sources anywhere
+    int src_nentry = 0;            // elements that carry a source (0: none)
+    int32_t* src_elem = nullptr;   // device [entries]
     int32_t* src_cand = nullptr;   // device [entries]
     void* src_w = nullptr;         // device Real [entries][MAXSRC][nsp]
     double *src_A = nullptr, *src_f = nullptr;  // device [ncand][MAXSRC]
@@ -101,8 +102,9 @@ namespace {
 template <typename Real>
 frk::Src<Real> src_of(const fr_ctx* c, double cfac) {
     frk::Src<Real> r;
-    if (!c->src_entry) return r;
-    r.entry = c->src_entry;
+    if (c->src_nentry <= 0) return r;
+    r.nentry = c->src_nentry;
+    r.elem = c->src_elem;
     r.cand = c->src_cand;
     r.w = static_cast<const Real*>(c->src_w);
     r.A = c->src_A;
@@ -210,6 +212,14 @@ int L_visc(fr_ctx* c, const Real* u, const Real* uf, cudaStream_t s) {
     ++c->launches;
     return c->dim == 2 ? frl::visc_face<Real, 2>(c->p, u, uf, fvn, c->E, op, ph, g, c->lc[1], s)
                        : frl::visc_face<Real, 3>(c->p, u, uf, fvn, c->E, op, ph, g, c->lc[1], s);
+}
+
+template <typename Real>
+int L_source(fr_ctx* c, const frk::Src<Real>& src, const frk::Stage<Real>& st, cudaStream_t s) {
+    ++c->launches;
+    const auto& op = ops_ref<Real>(c);
+    return c->dim == 2 ? frl::source_stage<Real, 2>(c->p, src, st, op, s)
+                       : frl::source_stage<Real, 3>(c->p, src, st, op, s);
 }
 
 template <typename Real>
@@ -341,13 +351,16 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         st.us = us;
         st.acc = acc;
         st.uf_next = uf_out;
-        st.src = src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5);
         if (pr) pr->mark_begin(2);
         rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
+        if (c->src_nentry > 0) {
+            rc = L_source<Real>(c, src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5), st, s);
+            CKL(rc, "source kernel");
+        }
     }
-    if (c->src_entry) {
+    if (c->src_nentry > 0) {
         k_time_advance<<<1, 32, 0, s>>>(c->tnow, c->dtc, c->ncand);
         ++c->launches;
         CK(cudaGetLastError());
@@ -373,9 +386,12 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     st.dte = nullptr;
     st.R = R;
     st.u0 = st.us = st.acc = st.uf_next = nullptr;
-    st.src = src_of<Real>(c, 0.0);
     rc = L_resid<Real>(c, u, uf, st, s);
     CKL(rc, "residual kernel");
+    if (c->src_nentry > 0) {
+        rc = L_source<Real>(c, src_of<Real>(c, 0.0), st, s);
+        CKL(rc, "source kernel");
+    }
     return FR_OK;
 }
 
@@ -437,7 +453,7 @@ void release(fr_ctx* c) {
     if (!c) return;
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
-                    c->fpart, c->src_entry, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc,
+                    c->fpart, c->src_elem, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc,
                     c->hlen, c->cand_off_d, c->lam};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -1007,15 +1023,16 @@ int upload_src_weights(fr_ctx* c, const std::vector<double>& w) {
 // Rebuilds the device source table from c->srcs: every element with a
 // solution point where some exp(-k_m |x - x_m|^2) exceeds 1e-30 gets an entry.
 int rebuild_sources(fr_ctx* c) {
-    for (void** b : {reinterpret_cast<void**>(&c->src_entry), reinterpret_cast<void**>(&c->src_cand), &c->src_w}) {
+    for (void** b : {reinterpret_cast<void**>(&c->src_elem), reinterpret_cast<void**>(&c->src_cand), &c->src_w}) {
         if (*b) cudaFree(*b);
         *b = nullptr;
     }
+    c->src_nentry = 0;
     bool any = false;
     for (const auto& v : c->srcs) any = any || !v.empty();
     if (!any) return FR_OK;
     const int dim = c->dim, nsp = c->nsp, nf = c->nf, nfp = c->nfp, M = frk::MAXSRC;
-    std::vector<int32_t> entry(size_t(c->E), -1), cand_of;
+    std::vector<int32_t> elem_of, cand_of;
     std::vector<double> w;
     std::vector<double> xyz(size_t(nsp) * dim), J(nsp), S(size_t(dim) * dim * nsp), N(size_t(nf) * nfp * dim);
     for (int k = 0; k < c->ncand; ++k) {
@@ -1040,7 +1057,7 @@ int rebuild_sources(fr_ctx* c) {
                     if (v > 1e-30) active = true;
                 }
             if (!active) continue;
-            entry[e] = int32_t(cand_of.size());
+            elem_of.push_back(int32_t(e));
             cand_of.push_back(k);
             w.insert(w.end(), we.begin(), we.end());
         }
@@ -1052,14 +1069,16 @@ int rebuild_sources(fr_ctx* c) {
             f[size_t(k) * M + m] = c->srcs[k][m][5];
         }
     int rc;
-    if ((rc = upload(reinterpret_cast<void**>(&c->src_entry), entry)) ||
-        (rc = upload(reinterpret_cast<void**>(&c->src_cand), cand_of.empty() ? std::vector<int32_t>{0} : cand_of)))
+    if (cand_of.empty()) return FR_OK;   // sources too far from every solution point
+    if ((rc = upload(reinterpret_cast<void**>(&c->src_elem), elem_of)) ||
+        (rc = upload(reinterpret_cast<void**>(&c->src_cand), cand_of)))
         return rc;
     rc = c->prec == FR_FP64 ? upload_src_weights<double>(c, w) : upload_src_weights<float>(c, w);
     if (rc) return rc;
     if (cudaMemcpy(c->src_A, A.data(), A.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->src_f, f.data(), f.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return FR_ECUDA;
+    c->src_nentry = int(cand_of.size());
     return FR_OK;
 }
 

@@ -62,24 +62,6 @@ struct Geo {
 //   stage 4: input us;  u0 = u0 + acc + dt/6 k4
 // uf_next (stages 1-4): traces of the stage's output state, for the next stage.
 // dte (optional): per-element time step overriding dt.
-// src (optional, entry == nullptr: none): energy source of Appendix D, Eq. D.1,
-//   s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi f_m t), added to the
-//   energy residual of the elements that carry one, at the stage time
-//   t = tnow[cand] + cfac * dt (cfac = 0, 1/2, 1/2, 1 for stages 1-4; 0 for
-//   stage 0).  entry[e] indexes the element's weights
-//   w[entry][m][sp] = exp(-k_m |x_sp - x_m|^2) (-1: none); A, f are per
-//   candidate [cand][MAXSRC] (unused slots A = 0).
-constexpr int MAXSRC = 4;
-template <typename Real>
-struct Src {
-    const int32_t* entry = nullptr;
-    const int32_t* cand = nullptr;
-    const Real* w = nullptr;
-    const double* A = nullptr;
-    const double* f = nullptr;
-    const double* tnow = nullptr;
-    double cfac = 0.0;
-};
 template <typename Real>
 struct Stage {
     int stage;
@@ -90,7 +72,25 @@ struct Stage {
     Real* us;
     Real* acc;
     Real* uf_next;
-    Src<Real> src{};
+};
+
+// Energy source of Appendix D, Eq. D.1,
+//   s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi f_m t),
+// for the nentry elements that carry one: elem[j], cand[j] and weights
+// w[j][m][sp] = exp(-k_m |x_sp - x_m|^2); A, f per candidate [cand][MAXSRC]
+// (unused slots A = 0); stage time t = tnow[cand] + cfac * dt (cfac = 0, 1/2,
+// 1/2, 1 for stages 1-4; 0 for stage 0).
+constexpr int MAXSRC = 4;
+template <typename Real>
+struct Src {
+    int nentry = 0;
+    const int32_t* elem = nullptr;
+    const int32_t* cand = nullptr;
+    const Real* w = nullptr;
+    const double* A = nullptr;
+    const double* f = nullptr;
+    const double* tnow = nullptr;
+    double cfac = 0.0;
 };
 
 // One warp per element; epb elements (warps) per block.
@@ -134,6 +134,11 @@ int sample(int P, const Real* u, const int64_t* pe, const Real* pw, int npts, co
 template <typename Real, int DIM>
 int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,
               const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
+
+// energy source share of one stage (Src above) for the source elements
+template <typename Real, int DIM>
+int source_stage(int P, const frk::Src<Real>& src, const frk::Stage<Real>& st, const frk::Ops<Real>& op,
+                 void* stream);
 
 // per-candidate maximum spectral rate of the adaptive time step (lam holds
 // the bits of non-negative doubles, zeroed by the caller)

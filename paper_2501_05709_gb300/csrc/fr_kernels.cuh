@@ -1034,7 +1034,6 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     // F: residual and RK stage per solution point; the new stage state
     // replaces su for the traces
     const Real dt = st.dte ? st.dte[e] : st.dt;
-    const int sx = st.src.entry ? st.src.entry[e] : -1;   // energy source entry (Eq. D.1), or none
 #pragma unroll
     for (int s = 0; s < NSPW; ++s) {
         const int sp = lane + 32 * s;
@@ -1043,18 +1042,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const int k = VL::pt(v, sp);
-            Real r = -sd[k] * iJ;
-            if (v == NV - 1 && sx >= 0) {
-                const int c = st.src.cand[sx];
-                const double t = st.src.tnow[c] + st.src.cfac * double(dt);
-#pragma unroll 1
-                for (int m = 0; m < MAXSRC; ++m) {
-                    const double a = st.src.A[c * MAXSRC + m];
-                    if (a != 0.0)
-                        r += Real(a * sinpi(2.0 * st.src.f[c * MAXSRC + m] * t)) *
-                             st.src.w[(int64_t(sx) * MAXSRC + m) * NSP + sp];
-                }
-            }
+            const Real r = -sd[k] * iJ;
             const int64_t gi = base + v * NSP + sp;
             Real u0v = Real(0), accv = Real(0);
             if (st.stage >= 2) {
@@ -1099,6 +1087,68 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
         __syncwarp();
         warp_write_traces<DIM, P>(su, st.uf_next + e * NF * NV * NFP, op, lane);
     }
+}
+
+// Energy source of Appendix D (Eq. D.1), applied after the residual kernel of
+// a stage to the few elements that carry one (warp per source entry).  The
+// RK4 update is linear in the residual, so adding the source's share to the
+// stage arrays afterwards equals adding it to R first: stage 0 adds s to R;
+// stages 1-4 add (dt/2, dt/2, dt, dt/6) s to the stage output (us, us, us,
+// u0) and (dt/6, dt/3, dt/3, -) s to acc, and, traces being linear in the
+// state, add the face traces of the state increment to the next traces.
+template <int DIM, int P, typename Real>
+__global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __grid_constant__ Stage<Real> st,
+                               const __grid_constant__ Ops<Real> op) {
+    using Z = Sz<DIM, P>;
+    constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    using VL = Vol<DIM, P, Real>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (j >= src.nentry) return;
+    Real* sdel = reinterpret_cast<Real*>(smem) + warp * NSP;   // state increment [sp] (volume placement)
+    const int64_t e = src.elem[j];
+    const int c = src.cand[j];
+    const double dt = double(st.dte ? st.dte[e] : st.dt);
+    const double t = src.tnow[c] + src.cfac * dt;
+    double amp[MAXSRC];
+#pragma unroll
+    for (int m = 0; m < MAXSRC; ++m) {
+        const double a = src.A[c * MAXSRC + m];
+        amp[m] = a != 0.0 ? a * sinpi(2.0 * src.f[c * MAXSRC + m] * t) : 0.0;
+    }
+    const double cs = st.stage == 3 ? dt : st.stage == 4 ? dt / 6.0 : 0.5 * dt;   // into the stage output
+    const double ca = st.stage == 1 ? dt / 6.0 : dt / 3.0;                       // into acc (stages 1-3)
+    const int64_t gbase = (e * NV + (NV - 1)) * NSP;                             // energy row
+    for (int sp = lane; sp < NSP; sp += 32) {
+        double sv = 0.0;
+#pragma unroll
+        for (int m = 0; m < MAXSRC; ++m) sv += amp[m] * double(src.w[(int64_t(j) * MAXSRC + m) * NSP + sp]);
+        if (st.stage == 0) {
+            st.R[gbase + sp] += Real(sv);
+            continue;
+        }
+        const Real du = Real(cs * sv);
+        if (st.stage == 4) {
+            st.u0[gbase + sp] += du;
+        } else {
+            st.us[gbase + sp] += du;
+            st.acc[gbase + sp] += Real(ca * sv);
+        }
+        sdel[VL::pt(0, sp)] = du;
+    }
+    if (st.stage == 0 || !st.uf_next) return;
+    __syncwarp();
+    // traces of the increment (one variable) added to the energy rows of the next traces
+    Real* uf = st.uf_next + e * NF * NV * NFP;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        for (int ln = lane; ln < NFP; ln += 32) {
+            Real m, p;
+            line_ends<DIM, P>(sdel, 0, op, d, ln, m, p);
+            uf[(2 * d * NV + NV - 1) * NFP + ln] += m;
+            uf[((2 * d + 1) * NV + NV - 1) * NFP + ln] += p;
+        }
 }
 
 // Adaptive time step (Section 3.1: adaptive time stepping): per element

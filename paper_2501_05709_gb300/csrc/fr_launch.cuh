@@ -159,6 +159,19 @@ int integrals<FR_REAL, FR_DIM>(int P, const FR_REAL* u, int64_t e_first, int64_t
 }
 
 template <>
+int source_stage<FR_REAL, FR_DIM>(int P, const frk::Src<FR_REAL>& src, const frk::Stage<FR_REAL>& st,
+                                  const frk::Ops<FR_REAL>& op, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (src.nentry <= 0) return 0;
+    const unsigned blocks = unsigned((src.nentry + 3) / 4);
+#define C(PP) (frk::k_source_stage<FR_DIM, PP, FR_REAL><<<blocks, 128,                                    \
+                   4 * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(src, st, op),                   \
+               int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
 int cfl<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* hlen, int64_t E, const int64_t* cand_off,
                          int ncand, const frk::Phys<FR_REAL>& ph, unsigned long long* lam, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
