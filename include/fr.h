@@ -251,7 +251,7 @@ int fwh_integrate(const double* hist, int nt, int npts, const double* y, const d
  * cudaMalloc/cudaFree, e.g. an application whose device memory is all owned
  * by its own pool allocator, or one that must not pay the device-wide
  * synchronisation of cudaFree in the middle of its work.
- *   - Limit: 8*npts*nt + ceil(npts / max(1, 1024/ncopies)) * (longest
+ *   - Limit: 8*npts*nt + ceil(npts / max(1, 32/ncopies)) * (longest
  *     observer window) must not exceed 2^22; larger problems get FR_EINVAL
  *     with a message naming the sizes (use fwh_integrate for them).
  *   - The first call on a device looks up the array's device address

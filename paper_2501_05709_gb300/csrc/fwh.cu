@@ -121,14 +121,34 @@ __device__ void panel_coefs(const double* y, double dS, const double* obs, const
     *delay = R / k.c0;
 }
 
+// Each thread accumulates FWH_KO consecutive observer-time samples over the
+// panel-copies of its block's group.  A panel-copy's stencil offset and cubic
+// weights are the same for every sample (t = tstart + i dtau advances the
+// source index by exactly 1 per sample), so they are computed once per block;
+// each source time j in the thread's window combines the 8 series once
+// (I_j = sum_v cf_v X_v(j)) and serves up to four samples.  Samples whose
+// stencil is clamped at the ends of the record take the general per-sample
+// path.  Small groups give many blocks per observer (the FP64 pipe needs the
+// parallelism).
+constexpr int FWH_KO = 4;
+constexpr int kFwhGroup = 32;      // panel-copies per block (groups of whole panels)
+constexpr int FWH_SH = NSER + 5;   // per panel-copy: cf[8], weights[4], source index of sample 0
+// dynamic shared memory per panel-copy: the doubles above, the offset of the
+// panel's series and the stencil start of sample 0 (integers, so that the
+// sample loop does no FP64 conversions)
+constexpr size_t FWH_SH_BYTES = sizeof(double) * FWH_SH + sizeof(int64_t) + sizeof(int);
+
 __global__ void k_fwh_accum(const double* __restrict__ X, int nt, int npts, const double* __restrict__ y,
                             const double* __restrict__ dS, FwhConst k, double ox, double oy, double oz,
                             double tstart, int T, int ncopies, double Lspan, int group,
                             double* __restrict__ partial) {
-    extern __shared__ double sh[];  // [group*ncopies][NSER + 1]
-    const int p0 = blockIdx.y * group;
+    extern __shared__ double sh[];  // [cap][FWH_SH] doubles, then int64 [cap], then int [cap]
+    const int p0 = blockIdx.x * group;     // grid x: panel groups, grid y: sample blocks
     const int np = min(group, npts - p0);
     const int npc = np * ncopies;
+    const int cap = group * ncopies;
+    int64_t* xoff = reinterpret_cast<int64_t*>(sh + size_t(cap) * FWH_SH);
+    int* jbs = reinterpret_cast<int*>(xoff + cap);
     const int K = (ncopies - 1) / 2;
     const double obs[3] = {ox, oy, oz};
     for (int w = threadIdx.x; w < npc; w += blockDim.x) {
@@ -136,37 +156,70 @@ __global__ void k_fwh_accum(const double* __restrict__ X, int nt, int npts, cons
         const int cc = w % ncopies - K;
         const double yy[3] = {y[p * 3 + 0], y[p * 3 + 1], y[p * 3 + 2] + cc * Lspan};
         double delay;
-        panel_coefs(yy, dS[p], obs, k, sh + w * (NSER + 1), &delay);
-        sh[w * (NSER + 1) + NSER] = (tstart - k.tau0 - delay) / k.dtau;
+        double* cf = sh + w * FWH_SH;
+        panel_coefs(yy, dS[p], obs, k, cf, &delay);
+        const double off = (tstart - k.tau0 - delay) / k.dtau;   // source index of sample 0
+        const double fl = floor(off);
+        const double x = off - fl + 1.0;                        // position in the stencil, [1, 2)
+        cf[NSER + 0] = -(x - 1.0) * (x - 2.0) * (x - 3.0) / 6.0;
+        cf[NSER + 1] = x * (x - 2.0) * (x - 3.0) / 2.0;
+        cf[NSER + 2] = -x * (x - 1.0) * (x - 3.0) / 2.0;
+        cf[NSER + 3] = x * (x - 1.0) * (x - 2.0) / 6.0;
+        cf[NSER + 4] = off;
+        jbs[w] = int(fl) - 1;
+        xoff[w] = int64_t(p) * NSER * nt;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T) return;
-    double acc = 0.0;
+    const int i0 = (blockIdx.y * blockDim.x + threadIdx.x) * FWH_KO;
+    if (i0 >= T) return;
+    double acc[FWH_KO];
+#pragma unroll
+    for (int q = 0; q < FWH_KO; ++q) acc[q] = 0.0;
+    const bool whole = i0 + FWH_KO <= T;
     for (int w = 0; w < npc; ++w) {
-        const double* cf = sh + w * (NSER + 1);
-        const double s = double(i) + cf[NSER];
-        int j0 = int(floor(s)) - 1;
-        j0 = max(0, min(nt - 4, j0));
-        const double x = s - double(j0);
-        // cubic Lagrange weights on nodes 0..3 at x
-        const double w0 = -(x - 1.0) * (x - 2.0) * (x - 3.0) / 6.0;
-        const double w1 = x * (x - 2.0) * (x - 3.0) / 2.0;
-        const double w2 = -x * (x - 1.0) * (x - 3.0) / 2.0;
-        const double w3 = x * (x - 1.0) * (x - 2.0) / 6.0;
-        const double wt[4] = {w0, w1, w2, w3};
-        const double* xp = X + int64_t(p0 + w / ncopies) * NSER * nt + j0;
-        double sum = 0.0;
+        const double* cf = sh + w * FWH_SH;
+        const int j0 = i0 + jbs[w];
+        const double* xp = X + xoff[w];
+        if (whole && j0 >= 0 && j0 + FWH_KO + 3 <= nt) {
+            double c[FWH_KO + 3];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            double Ik = 0.0;
+            for (int m = 0; m < FWH_KO + 3; ++m) {
+                double Ik = 0.0;
 #pragma unroll
-            for (int v = 0; v < NSER; ++v) Ik += cf[v] * xp[v * nt + m];
-            sum += wt[m] * Ik;
+                for (int v = 0; v < NSER; ++v) Ik += cf[v] * xp[v * nt + j0 + m];
+                c[m] = Ik;
+            }
+#pragma unroll
+            for (int q = 0; q < FWH_KO; ++q) {
+                double sum = 0.0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) sum += cf[NSER + m] * c[q + m];
+                acc[q] += sum;
+            }
+        } else {
+            const double off = cf[NSER + 4];
+            for (int q = 0; q < FWH_KO && i0 + q < T; ++q) {
+                const double s = double(i0 + q) + off;
+                int j = int(floor(s)) - 1;
+                j = max(0, min(nt - 4, j));
+                const double x = s - double(j);
+                const double wt[4] = {-(x - 1.0) * (x - 2.0) * (x - 3.0) / 6.0, x * (x - 2.0) * (x - 3.0) / 2.0,
+                                      -x * (x - 1.0) * (x - 3.0) / 2.0, x * (x - 1.0) * (x - 2.0) / 6.0};
+                double sum = 0.0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    double Ik = 0.0;
+#pragma unroll
+                    for (int v = 0; v < NSER; ++v) Ik += cf[v] * xp[v * nt + j + m];
+                    sum += wt[m] * Ik;
+                }
+                acc[q] += sum;
+            }
         }
-        acc += sum;
     }
-    partial[int64_t(blockIdx.y) * T + i] = acc;
+#pragma unroll
+    for (int q = 0; q < FWH_KO; ++q)
+        if (i0 + q < T) partial[int64_t(blockIdx.x) * T + i0 + q] = acc[q];
 }
 
 __global__ void k_fwh_reduce(const double* __restrict__ partial, int ngroups, int T, double* __restrict__ out) {
@@ -234,9 +287,10 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
         tstart[o] = ts;
         Tn[o] = T;
     }
-    const int group = std::max(1, 1024 / ncopies);
+    const int group = std::max(1, kFwhGroup / ncopies);
     const int ngroups = (npts + group - 1) / group;
-    if (ngroups > 65535) return fr_set_error_from_fwh(FR_EINVAL, "too many panels for one launch");
+    if ((cap + 128 * FWH_KO - 1) / (128 * FWH_KO) > 65535)
+        return fr_set_error_from_fwh(FR_EINVAL, "observer window too long for one launch");
     int Tmax = *std::max_element(Tn.begin(), Tn.end());
     double *X = nullptr, *partial = nullptr;
     if (cudaMalloc(&X, sizeof(double) * size_t(npts) * NSER * nt) != cudaSuccess ||
@@ -246,13 +300,13 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
     }
     const int64_t nw = int64_t(nt) * npts;
     k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
-    const size_t sm = sizeof(double) * size_t(group) * ncopies * (NSER + 1);
+    const size_t sm = FWH_SH_BYTES * size_t(group) * ncopies;
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess && sm > 48 * 1024)
         err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
-        dim3 grid(unsigned((Tn[o] + 255) / 256), unsigned(ngroups));
-        k_fwh_accum<<<grid, 256, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
+        dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
+        k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
                                           tstart[o], Tn[o], ncopies, Lspan, group, partial);
         k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
         err = cudaGetLastError();
@@ -354,9 +408,10 @@ extern "C" int fwh_integrate_noalloc(const double* hist, int nt, int npts, const
         tstart[o] = ts;
         Tn[o] = T;
     }
-    const int group = std::max(1, 1024 / ncopies);
+    const int group = std::max(1, kFwhGroup / ncopies);
     const int ngroups = (npts + group - 1) / group;
-    if (ngroups > 65535) return fr_set_error_from_fwh(FR_EINVAL, "too many panels for one launch");
+    if ((cap + 128 * FWH_KO - 1) / (128 * FWH_KO) > 65535)
+        return fr_set_error_from_fwh(FR_EINVAL, "observer window too long for one launch");
     const int Tmax = *std::max_element(Tn.begin(), Tn.end());
     // the series (8 per panel and source time) and one partial row per panel
     // group must fit the fixed scratch; both are fully written before any read
@@ -365,20 +420,20 @@ extern "C" int fwh_integrate_noalloc(const double* hist, int nt, int npts, const
         return fr_set_error_from_fwh(
             FR_EINVAL, ("fwh_integrate_noalloc: needs " + std::to_string(need) + " doubles of scratch, the fixed "
                         "maximum is " + std::to_string(kNoallocScratchDoubles) +
-                        " (8*npts*nt + ceil(npts/max(1,1024/ncopies))*window); use fwh_integrate").c_str());
+                        " (8*npts*nt + ceil(npts/max(1,32/ncopies))*window); use fwh_integrate").c_str());
     double* X = nullptr;
     const int rc = noalloc_scratch(&X);
     if (rc != FR_OK) return rc;
     double* partial = X + size_t(npts) * NSER * nt;
     const int64_t nw = int64_t(nt) * npts;
     k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
-    const size_t sm = sizeof(double) * size_t(group) * ncopies * (NSER + 1);
+    const size_t sm = FWH_SH_BYTES * size_t(group) * ncopies;
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess && sm > 48 * 1024)
         err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
-        dim3 grid(unsigned((Tn[o] + 255) / 256), unsigned(ngroups));
-        k_fwh_accum<<<grid, 256, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
+        dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
+        k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
                                           tstart[o], Tn[o], ncopies, Lspan, group, partial);
         k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
         err = cudaGetLastError();
