@@ -156,14 +156,15 @@ class Clocks:
 # ----------------------------------------------------------------------------- ncu counters
 KERNEL_SOURCES = ("csrc/fr_kernels.cuh", "csrc/fr_common.h", "csrc/fr_launch.cuh", "csrc/fr_f32_3d.cu",
                   "csrc/fr_f64_3d.cu", "build.py")
+FWH_SOURCES = ("csrc/fwh.cu", "build.py")
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=KERNEL_SOURCES):
     """sha256 (first 16 hex digits) of the kernel sources and build flags:
     counters taken on other sources are stale and are not reported."""
     import hashlib
     h = hashlib.sha256()
-    for n in KERNEL_SOURCES:
+    for n in files:
         with open(os.path.join(ROOT, "paper_2501_05709_gb300", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -177,7 +178,7 @@ def ncu_counter(workload, precision, kernel, key):
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(FWH_SOURCES if kernel.startswith("fwh") else KERNEL_SOURCES)
     for ln in lines:
         if ln.startswith("#") or "=" not in ln:
             continue
@@ -493,10 +494,20 @@ def fwh_leg():
     torch.cuda.synchronize()
     t_psd = time.perf_counter() - t0
     work = len(y) * len(obs) * 3 * nt
+    # FP64-bound: executed FP64 flops of one call (ncu, all FW-H kernels)
+    # against the FP64 FMA rate measured on this GPU; the time is the whole call
+    fl = ncu_counter("fwh_directivity", "fp64", "fwh_integrate", "fp64_flops_per_call")
+    pk = F.fr_probe_fp64_peak()
+    ach = fl / t_int / 1e9 if fl else None
     return {"panels": int(len(y)), "observers": int(len(obs)), "copies": 3, "samples": nt,
             "window_samples_min": nmin, "fwh_integrate_ms": 1e3 * t_int,
             "panel_observer_copy_samples_per_s": work / t_int, "fwh_psd_ms": 1e3 * t_psd,
-            "note": "host wall time around each call (each call synchronises and includes its scratch set-up)"}
+            "roofline": {"bound": "alu", "kernel": "fwh_integrate (k_fwh_series + k_fwh_accum + k_fwh_reduce), FP64",
+                         "achieved": ach, "peak": pk, "unit": "GFLOP/s", "frac": ach / pk if ach else None,
+                         "flops_per_call": fl,
+                         "peak_source": "measured: FP64 FMA throughput probe (fr_probe_fp64_peak) on this GPU"},
+            "note": "host wall time around each call (each call synchronises and includes its scratch set-up "
+                    "and the host-side observer windows)"}
 
 
 def main():

@@ -222,12 +222,22 @@ __global__ void k_fwh_accum(const double* __restrict__ X, int nt, int npts, cons
         if (i0 + q < T) partial[int64_t(blockIdx.x) * T + i0 + q] = acc[q];
 }
 
+// p'(t_i) = (1/4 pi) sum over panel groups of the partial sums: 32 samples x
+// 32 group slices per block, each slice summing groups g = slice (mod 32) in
+// order, then a fixed-order tree over the slices (the same order every call)
 __global__ void k_fwh_reduce(const double* __restrict__ partial, int ngroups, int T, double* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T) return;
+    __shared__ double red[32][33];
+    const int i = blockIdx.x * 32 + threadIdx.x;
     double s = 0.0;
-    for (int g = 0; g < ngroups; ++g) s += partial[int64_t(g) * T + i];
-    out[i] = s / (4.0 * M_PI);
+    if (i < T)
+        for (int g = threadIdx.y; g < ngroups; g += 32) s += partial[int64_t(g) * T + i];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 16; st > 0; st >>= 1) {
+        if (threadIdx.y < st) red[threadIdx.y][threadIdx.x] += red[threadIdx.y + st][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.y == 0 && i < T) out[i] = red[0][threadIdx.x] / (4.0 * M_PI);
 }
 
 }  // namespace
@@ -308,7 +318,8 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
         dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
         k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
                                           tstart[o], Tn[o], ncopies, Lspan, group, partial);
-        k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
+        k_fwh_reduce<<<unsigned((Tn[o] + 31) / 32), dim3(32, 32), 0, s>>>(partial, ngroups, Tn[o],
+                                                                          p_out + size_t(o) * cap);
         err = cudaGetLastError();
         nt_out[o] = Tn[o];
         t0_out[o] = tstart[o];
@@ -435,7 +446,8 @@ extern "C" int fwh_integrate_noalloc(const double* hist, int nt, int npts, const
         dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
         k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
                                           tstart[o], Tn[o], ncopies, Lspan, group, partial);
-        k_fwh_reduce<<<unsigned((Tn[o] + 255) / 256), 256, 0, s>>>(partial, ngroups, Tn[o], p_out + size_t(o) * cap);
+        k_fwh_reduce<<<unsigned((Tn[o] + 31) / 32), dim3(32, 32), 0, s>>>(partial, ngroups, Tn[o],
+                                                                          p_out + size_t(o) * cap);
         err = cudaGetLastError();
         nt_out[o] = Tn[o];
         t0_out[o] = tstart[o];
