@@ -93,3 +93,20 @@ def test_fwh_integrate_rejects_bad_sizes_on_host(lib):
     rc = lib.fwh_integrate(p, 8, 1, p, p, p, 0.1, 0.0, p, 1, C.c_void_p(M2.ctypes.data), 340.0, 1.2, 1e5, 0.0,
                            1, p, 4, C.c_void_p(nt_out.ctypes.data), C.c_void_p(t0.ctypes.data), None)
     assert rc == F.FR_EINVAL
+
+
+def test_new_entry_points_reject_bad_input_on_host(lib):
+    # argument checks that run before any device work
+    z = np.zeros(64)
+    p = C.c_void_p(z.ctypes.data)
+    nf = C.c_int()
+    assert lib.fwh_psd(None, 1, 16, 16, 0.1, 3, p, 16, C.byref(nf), None) == F.FR_EINVAL
+    assert lib.fwh_psd(p, 1, 3, 3, 0.1, 3, p, 16, C.byref(nf), None) == F.FR_EINVAL      # record too short
+    assert lib.fwh_psd(p, 1, 16, 8, 0.1, 3, p, 16, C.byref(nf), None) == F.FR_EINVAL     # ld < nt
+    assert lib.fwh_psd(p, 1, 16, 16, 0.0, 3, p, 16, C.byref(nf), None) == F.FR_EINVAL    # dt <= 0
+    assert lib.fwh_psd(p, 1, 16, 16, 0.1, 3, p, 2, C.byref(nf), None) == F.FR_EINVAL     # cap < L/2 + 1
+    t = C.c_double()
+    assert lib.fr_set_source(None, 0, 0, None, 0.0) == F.FR_EINVAL
+    assert lib.fr_source_time(None, 0, C.byref(t)) == F.FR_EINVAL
+    assert lib.fr_set_adaptive_dt(None, 0.5) == F.FR_EINVAL
+    assert lib.fr_cand_dt(None, 0, C.byref(t)) == F.FR_EINVAL
