@@ -425,6 +425,52 @@ struct LineTask {
     }
 };
 
+// q[i] += sum_j D[i][j] s[j].  For p = 3 in FP32 the four rows go as two
+// packed pairs (two FP32 FMAs per instruction, the same order of operations).
+template <int NP, typename Real>
+__device__ __forceinline__ void apply_D(const Ops<Real>& op, const Real (&s)[NP], Real (&q)[NP]) {
+    if constexpr (NP == 4 && sizeof(Real) == 4) {
+        float2 a = make_float2(q[0], q[1]), b = make_float2(q[2], q[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 sj = make_float2(s[j], s[j]);
+            a = __ffma2_rn(make_float2(op.D[0 * MAXNP + j], op.D[1 * MAXNP + j]), sj, a);
+            b = __ffma2_rn(make_float2(op.D[2 * MAXNP + j], op.D[3 * MAXNP + j]), sj, b);
+        }
+        q[0] = a.x;
+        q[1] = a.y;
+        q[2] = b.x;
+        q[3] = b.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) q[i] += op.D[i * MAXNP + j] * s[j];
+    }
+}
+
+// m = sum_j l_j(-1) s_j and p = sum_j l_j(+1) s_j of a line held in
+// registers; in FP32 as one packed pair (same order of operations)
+template <int NP, typename Real>
+__device__ __forceinline__ void ends_of(const Ops<Real>& op, const Real (&s)[NP], Real& m, Real& p) {
+    if constexpr (sizeof(Real) == 4) {
+        float2 mp = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            mp = __ffma2_rn(make_float2(op.lm[j], op.lm[NP - 1 - j]), make_float2(s[j], s[j]), mp);
+        m = mp.x;
+        p = mp.y;
+    } else {
+        m = Real(0);
+        p = Real(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            m += op.lm[j] * s[j];
+            p += op.lm[NP - 1 - j] * s[j];
+        }
+    }
+}
+
 // both end values of line ln (direction d) of variable v of volume array X:
 // m = sum_j l_j(-1) s_j and p = sum_j l_j(+1) s_j
 template <int DIM, int P, typename Real>
@@ -433,13 +479,7 @@ __device__ __forceinline__ void line_ends(const Real* X, int v, const Ops<Real>&
     constexpr int NP = P + 1;
     Real s[NP];
     vload_line<DIM, P>(X, v, d, ln, s);
-    m = Real(0);
-    p = Real(0);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        m += op.lm[j] * s[j];
-        p += op.lm[NP - 1 - j] * s[j];
-    }
+    ends_of<NP>(op, s, m, p);
 }
 
 // ---- cp.async staging (global -> shared without registers)
@@ -516,6 +556,33 @@ __device__ __forceinline__ Real trace_at(const Real* X, int v, int d, int fp, co
 #pragma unroll
     for (int j = 0; j < P + 1; ++j) acc += c[j] * s[j];
     return acc;
+}
+
+// the traces of the NVV variables 0..NVV-1 of X on one face point; in FP32 two
+// variables per packed FMA (the same order of operations as trace_at)
+template <int DIM, int P, int NVV, typename Real>
+__device__ __forceinline__ void traces_at(const Real* X, int d, int fp, const Real (&c)[P + 1], Real (&tr)[NVV]) {
+    constexpr int NP = P + 1;
+    if constexpr (sizeof(Real) == 4) {
+        float2 cc[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) cc[j] = make_float2(c[j], c[j]);
+#pragma unroll
+        for (int k = 0; k + 1 < NVV; k += 2) {
+            Real s0[NP], s1[NP];
+            vload_line<DIM, P>(X, k, d, fp, s0);
+            vload_line<DIM, P>(X, k + 1, d, fp, s1);
+            float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) a = __ffma2_rn(cc[j], make_float2(s0[j], s1[j]), a);
+            tr[k] = a.x;
+            tr[k + 1] = a.y;
+        }
+        if constexpr (NVV % 2 == 1) tr[NVV - 1] = trace_at<DIM, P>(X, NVV - 1, d, fp, c);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NVV; ++k) tr[k] = trace_at<DIM, P>(X, k, d, fp, c);
+    }
 }
 
 // traces of the element state su at every flux point -> ufe [NF][NV][NFP]
@@ -652,11 +719,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             Real s[NP], q[NP];
             vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                q[i] = Real(0);
-#pragma unroll
-                for (int j = 0; j < NP; ++j) q[i] += op.D[i * MAXNP + j] * s[j];
-            }
+            for (int i = 0; i < NP; ++i) q[i] = Real(0);
+            apply_D<NP>(op, s, q);
             vstore_line<DIM, P>(sg + tk.shift, d * NV + tk.vref, d, tk.ln, q);
         }
     }
@@ -737,6 +801,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
             }
+            Real tr[DIM * NV];   // traces of the physical gradient [i][v]
+            traces_at<DIM, P, DIM * NV>(sg, d, fp, cf, tr);
             Real G[NV][DIM];
             Real uL[NV];
 #pragma unroll
@@ -744,8 +810,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 const Real jv = sj[(f * NV + v) * NFP + fp];
                 uL[v] = sl[(f * NV + v) * NFP + fp];
 #pragma unroll
-                for (int i = 0; i < DIM; ++i)
-                    G[v][i] = trace_at<DIM, P>(sg, i * NV + v, d, fp, cf) + ph.eta * lc[i] * jv;
+                for (int i = 0; i < DIM; ++i) G[v][i] = tr[i * NV + v] + ph.eta * lc[i] * jv;
             }
             const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
@@ -925,11 +990,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
                 const Real jL = sj[2 * d * NV * NFP + tk.t];
                 const Real jR = sj[(2 * d + 1) * NV * NFP + tk.t];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    q[i] = op.hm[NP - 1 - i] * jR - op.hm[i] * jL;
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) q[i] += op.D[i * MAXNP + j] * s[j];
-                }
+                for (int i = 0; i < NP; ++i) q[i] = op.hm[NP - 1 - i] * jR - op.hm[i] * jL;
+                apply_D<NP>(op, s, q);
                 vstore_line<DIM, P>(sF + tk.shift, d * NV + tk.vref, d, tk.ln, q);
             }
         }
@@ -1006,21 +1068,14 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             if (NL % 32 != 0 && tk.t >= NL) break;
             Real s[NP];
             vload_line<DIM, P>(sF + tk.shift, d * NV + tk.vref, d, tk.ln, s);
-            Real m = Real(0), pp = Real(0);
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                m += op.lm[j] * s[j];
-                pp += op.lm[NP - 1 - j] * s[j];
-            }
+            Real m, pp;
+            ends_of<NP>(op, s, m, pp);
             const Real cL = sc[2 * d * NV * NFP + tk.t] + m;
             const Real cR = sc[(2 * d + 1) * NV * NFP + tk.t] - pp;
             Real val[NP];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                val[i] = op.hm[i] * cL + op.hm[NP - 1 - i] * cR;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) val[i] += op.D[i * MAXNP + j] * s[j];
-            }
+            for (int i = 0; i < NP; ++i) val[i] = op.hm[i] * cL + op.hm[NP - 1 - i] * cR;
+            apply_D<NP>(op, s, val);
             if (d > 0) {
                 Real prev[NP];
                 vload_line<DIM, P>(sd + tk.shift, tk.vref, d, tk.ln, prev);
