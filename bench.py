@@ -160,13 +160,18 @@ FWH_SOURCES = ("csrc/fwh.cu", "build.py")
 
 
 def kernel_source_hash(files=KERNEL_SOURCES):
-    """sha256 (first 16 hex digits) of the kernel sources and build flags:
-    counters taken on other sources are stale and are not reported."""
+    """sha256 (first 16 hex digits) of the kernel sources and build flags,
+    without blank lines and whole-line comments: counters taken on other code
+    are stale and are not reported."""
     import hashlib
     h = hashlib.sha256()
     for n in files:
-        with open(os.path.join(ROOT, "paper_2501_05709_gb300", n), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2501_05709_gb300", n)) as f:
+            for line in f:
+                t = line.strip()
+                if t and not t.startswith(("//", "#")) or t.startswith(("#include", "#define", "#pragma", "#if",
+                                                                        "#else", "#endif", "#undef")):
+                    h.update(t.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -1,12 +1,16 @@
 // Flux Reconstruction kernels for sm_103a, templated on dimension, order and
-// precision.  One thread block processes a tile of `epb` whole elements; the
-// element data are staged in shared memory and every phase is a block-wide
-// loop over solution points or face points, separated by __syncthreads().
+// precision.  One warp processes one element (a block holds `epb` warps); the
+// element's data are staged in that warp's shared memory with cp.async, every
+// operator is applied along lines of solution points, and the phases of a
+// kernel are separated by __syncwarp() only.
 //
-// Per RK stage three sweeps (the two BR2 neighbour dependencies force them):
-//   k_traces     u            -> u_f (flux-point traces, written for neighbours)
+// Per RK stage two sweeps (the two BR2 neighbour dependencies force them):
 //   k_visc_face  u, u_f(nbr)  -> own-side viscous normal flux at flux points
-//   k_residual   u, u_f(nbr), viscous fluxes(own, nbr) -> R, fused RK4 stage
+//   k_residual   u, u_f(nbr), viscous fluxes(own, nbr) -> R, fused RK4 stage,
+//                and the flux-point traces u_f of the stage's output state
+// k_traces writes u_f only after the state is set from outside.  Smaller
+// kernels: wall forces, surface sampling, volume integrals, the energy source
+// of Appendix D and the adaptive time step.
 // Notation and steps follow Section 2.1 (Eqs. 1-7) with the FR reading
 // described in fr_common.h / fr.h: GL points, DG or g2 correction, Rusanov,
 // BR2, metric terms S = |J| dxi/dx in conservative-curl form.
