@@ -10,7 +10,11 @@
  *   - mean lift/drag, Section 3.2 (Table 1) and Eq. 8;
  *   - data-surface sampling of rho, p, velocity, Section 3.1 and 3.4;
  *   - FW-H moving-medium integration with spanwise duplication, Appendix B
- *     (Eqs. B.1-B.14) and Section 3.3.1.
+ *     (Eqs. B.1-B.14) and Section 3.3.1;
+ *   - Welch power spectral density of the observer pressure, Section 3.3;
+ *   - the energy source of the monopole validation cases, Appendix D
+ *     (Eq. D.1);
+ *   - adaptive time-step size, Section 3.1 (the integrator stays RK4).
  * FR details the paper leaves open are fixed as: Gauss-Legendre solution and
  * flux points, DG or Huynh-g2 correction functions, Rusanov inviscid flux,
  * BR2 viscous flux, classic four-stage RK4.
