@@ -56,15 +56,18 @@ def _expand(fv, h, d, dim, Np):
 class FRSolver:
     """Residual, RK4 and forces on one mesh for one physics.
 
+    ``caps``: optional per-element polynomial order caps (``oracle.sponge``).
     ``source``: optional list of Gaussian monopoles (A, k, (xs, ys, zs), freq)
     added to the energy equation (Appendix D, Eq. D.1):
     s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi freq_m t), evaluated at
     the solution points at the stage time."""
 
-    def __init__(self, mesh, phys, source=None):
+    def __init__(self, mesh, phys, source=None, caps=None):
         self.m = mesh
         self.ph = phys
         self.source = list(source) if source else []
+        # per-element order caps (``oracle.sponge``): R <- Pi_q R on elements with q < p
+        self.caps = None if caps is None else np.asarray(caps, np.int64)
 
     def source_term(self, t):
         """s(x_sp, t) [E, Nsp] of Eq. D.1 (zeros without sources)."""
@@ -189,6 +192,9 @@ class FRSolver:
         R = -div.reshape(E, nv, -1) / J[:, None]
         if self.source:
             R[:, nv - 1, :] += self.source_term(t)
+        if self.caps is not None:
+            from .sponge import project
+            R = project(m, R, self.caps)
         if not want_faces:
             return R
         return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc}
