@@ -14,7 +14,9 @@
  *   - Welch power spectral density of the observer pressure, Section 3.3;
  *   - the energy source of the monopole validation cases, Appendix D
  *     (Eq. D.1);
- *   - adaptive time-step size, Section 3.1 (the integrator stays RK4).
+ *   - adaptive time-step size, Section 3.1 (the integrator stays RK4);
+ *   - variable polynomial order by element (the sponge zones of
+ *     Section 3.1).
  * FR details the paper leaves open are fixed as: Gauss-Legendre solution and
  * flux points, DG or Huynh-g2 correction functions, Rusanov inviscid flux,
  * BR2 viscous flux, classic four-stage RK4.
@@ -129,8 +131,9 @@ int fr_cand_range(const fr_ctx* ctx, int cand, int64_t* first, int64_t* count);
 
 /* State upload / download in the canonical layout as double.  cand < 0
  * addresses the whole batch.  on_device != 0: u is a device pointer.
- * fr_state_set also resets the RK stage buffers.  The call synchronises the
- * given stream before returning. */
+ * fr_state_set also resets the RK stage buffers and projects elements of
+ * reduced degree (fr_set_element_order).  The call synchronises the given
+ * stream before returning. */
 int fr_state_set(fr_ctx* ctx, int cand, const double* u, int on_device, void* stream);
 int fr_state_get(fr_ctx* ctx, int cand, double* u, int on_device, void* stream);
 
@@ -189,6 +192,23 @@ int fr_set_adaptive_dt(fr_ctx* ctx, double cfl);
 
 /* The candidate's current step (the last adaptive one, or the fixed one). */
 int fr_cand_dt(const fr_ctx* ctx, int cand, double* dt);
+
+/* Variable polynomial order (Section 3.1: the solution degree drops from the
+ * context's p near the body to 0 in the outer rings, so that the coarse,
+ * low-order far field absorbs outgoing waves).  order[i] in 0..p is the degree
+ * of element i of candidate cand (cand = -1: of the whole batch, E entries);
+ * order = NULL gives the candidate's elements p again.  Every element keeps
+ * the context's (p+1)^dim points; an element of degree q < p holds its
+ * solution in the tensor-product polynomials of degree q: its residual is
+ * replaced by the L2 projection onto that space (the 1D projection
+ *   Pi_q[i][j] = sum_{k<=q} P_k(x_i) P_k(x_j) w_j (2k+1)/2,
+ * P_k Legendre, x, w the GL points and weights, along each direction), and
+ * the current state and every state set later are projected the same way.
+ * The projection keeps each element's mean, so conservation holds on affine
+ * elements.  Errors: FR_EINVAL (cand out of range, an order outside 0..p),
+ * FR_ENOMEM.  Synchronises the device; rebuilds the step's CUDA graph on its
+ * next replay. */
+int fr_set_element_order(fr_ctx* ctx, int cand, const int32_t* order);
 
 /* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
  * use for the current surfaces and options).  Bit-identical results. */

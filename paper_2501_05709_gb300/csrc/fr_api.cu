@@ -95,6 +95,11 @@ struct fr_ctx {
     void* hlen = nullptr;                // device Real [E]: element length
     int64_t* cand_off_d = nullptr;       // device [ncand + 1]
     unsigned long long* lam = nullptr;   // device [ncand]: max spectral rate (double bits)
+    // variable polynomial order (sponge zones), see frk::Sponge
+    std::vector<std::vector<int32_t>> order;  // per candidate: [count] degree caps (empty: all p)
+    int sp_n = 0;                             // capped elements (0: none)
+    int32_t *sp_elem = nullptr, *sp_cap = nullptr;  // device [sp_n]
+    std::vector<int> sp_off;                  // [ncand + 1]: each candidate's slice of the list
 };
 
 namespace {
@@ -220,6 +225,45 @@ int L_source(fr_ctx* c, const frk::Src<Real>& src, const frk::Stage<Real>& st, c
     const auto& op = ops_ref<Real>(c);
     return c->dim == 2 ? frl::source_stage<Real, 2>(c->p, src, st, op, s)
                        : frl::source_stage<Real, 3>(c->p, src, st, op, s);
+}
+
+// the 1D projections onto degree q = 0..p on the GL points,
+// Pi_q[i][j] = sum_{k <= q} P_k(x_i) P_k(x_j) w_j (2k + 1) / 2
+template <typename Real>
+frk::Sponge<Real> sponge_of(const fr_ctx* c) {
+    frk::Sponge<Real> r;
+    r.n = c->sp_n;
+    r.elem = c->sp_elem;
+    r.cap = c->sp_cap;
+    const int np = c->np;
+    double L[frk::MAXNP][frk::MAXNP], dL[frk::MAXNP];
+    for (int i = 0; i < np; ++i) frg::legendre(np - 1, c->ref.x[i], L[i], dL);
+    for (int q = 0; q < frk::MAXNP; ++q)
+        for (int i = 0; i < frk::MAXNP; ++i)
+            for (int j = 0; j < frk::MAXNP; ++j) {
+                double v = 0.0;
+                if (i < np && j < np)
+                    for (int k = 0; k <= q && k < np; ++k) v += L[i][k] * L[j][k] * c->ref.w[j] * (2 * k + 1) * 0.5;
+                r.pm[q][i * frk::MAXNP + j] = Real(v);
+            }
+    return r;
+}
+
+// cand >= 0: that candidate's capped elements only
+template <typename Real>
+int L_sponge(fr_ctx* c, Real* a, Real* b, Real* uf_out, cudaStream_t s, int cand = -1) {
+    if (c->sp_n <= 0) return 0;
+    auto sp = sponge_of<Real>(c);
+    if (cand >= 0) {
+        sp.elem += c->sp_off[cand];
+        sp.cap += c->sp_off[cand];
+        sp.n = c->sp_off[cand + 1] - c->sp_off[cand];
+        if (sp.n == 0) return 0;
+    }
+    ++c->launches;
+    const auto& op = ops_ref<Real>(c);
+    return c->dim == 2 ? frl::sponge<Real, 2>(c->p, sp, a, b, uf_out, op, s)
+                       : frl::sponge<Real, 3>(c->p, sp, a, b, uf_out, op, s);
 }
 
 template <typename Real>
@@ -359,6 +403,10 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             rc = L_source<Real>(c, src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5), st, s);
             CKL(rc, "source kernel");
         }
+        if (c->sp_n > 0) {
+            rc = stage == 4 ? L_sponge<Real>(c, u0, nullptr, uf_out, s) : L_sponge<Real>(c, us, acc, uf_out, s);
+            CKL(rc, "sponge kernel");
+        }
     }
     if (c->src_nentry > 0) {
         k_time_advance<<<1, 32, 0, s>>>(c->tnow, c->dtc, c->ncand);
@@ -391,6 +439,10 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     if (c->src_nentry > 0) {
         rc = L_source<Real>(c, src_of<Real>(c, 0.0), st, s);
         CKL(rc, "source kernel");
+    }
+    if (c->sp_n > 0) {
+        rc = L_sponge<Real>(c, R, nullptr, nullptr, s);
+        CKL(rc, "sponge kernel");
     }
     return FR_OK;
 }
@@ -454,7 +506,7 @@ void release(fr_ctx* c) {
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
                     c->fpart, c->src_elem, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc,
-                    c->hlen, c->cand_off_d, c->lam};
+                    c->hlen, c->cand_off_d, c->lam, c->sp_elem, c->sp_cap};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -878,6 +930,11 @@ extern "C" int fr_state_set(fr_ctx* c, int cand, const double* u, int on_device,
         ++c->launches;
         CK(cudaGetLastError());
     }
+    if (c->sp_n > 0) {
+        rc = c->prec == FR_FP64 ? L_sponge<double>(c, static_cast<double*>(c->u0), nullptr, nullptr, s, cand)
+                                : L_sponge<float>(c, static_cast<float*>(c->u0), nullptr, nullptr, s, cand);
+        CKL(rc, "sponge kernel");
+    }
     CK(cudaStreamSynchronize(s));
     return FR_OK;
 }
@@ -1114,6 +1171,58 @@ extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, d
     c->srcs[cand] = sv;
     const int rc = rebuild_sources(c);
     if (rc) return fail(rc, "cannot build the source table");
+    invalidate_graph(c);
+    CK(cudaDeviceSynchronize());
+    return FR_OK;
+}
+
+extern "C" int fr_set_element_order(fr_ctx* c, int cand, const int32_t* order) {
+    if (!c || cand < -1 || cand >= c->ncand) return fail(FR_EINVAL, "bad argument");
+    const int k0 = cand < 0 ? 0 : cand, k1 = cand < 0 ? c->ncand : cand + 1;
+    if (order) {
+        const int64_t n = c->cand_off[k1] - c->cand_off[k0];
+        for (int64_t i = 0; i < n; ++i)
+            if (order[i] < 0 || order[i] > c->p) return fail(FR_EINVAL, "element order outside 0..p");
+    }
+    CK(cudaDeviceSynchronize());
+    if (c->order.empty()) c->order.resize(c->ncand);
+    for (int k = k0; k < k1; ++k) {
+        const int64_t a0 = c->cand_off[k], n = c->cand_off[k + 1] - a0;
+        if (order) c->order[k].assign(order + (a0 - c->cand_off[k0]), order + (a0 - c->cand_off[k0]) + n);
+        else c->order[k].clear();
+    }
+    // the device list: (element, cap) of every element with cap < p, by candidate
+    std::vector<int32_t> el, cp;
+    c->sp_off.assign(c->ncand + 1, 0);
+    for (int k = 0; k < c->ncand; ++k) {
+        for (size_t i = 0; i < c->order[k].size(); ++i)
+            if (c->order[k][i] < c->p) {
+                el.push_back(int32_t(c->cand_off[k] + int64_t(i)));
+                cp.push_back(c->order[k][i]);
+            }
+        c->sp_off[k + 1] = int(el.size());
+    }
+    for (int32_t** b : {&c->sp_elem, &c->sp_cap}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    c->sp_n = 0;
+    if (!el.empty()) {
+        const size_t bytes = el.size() * sizeof(int32_t);
+        if (cudaMalloc(&c->sp_elem, bytes) != cudaSuccess || cudaMalloc(&c->sp_cap, bytes) != cudaSuccess)
+            return fail(FR_ENOMEM, "cannot allocate the element order table");
+        CK(cudaMemcpy(c->sp_elem, el.data(), bytes, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->sp_cap, cp.data(), bytes, cudaMemcpyHostToDevice));
+        c->sp_n = int(el.size());
+        // the current state of the changed candidates moves into the capped spaces
+        for (int k = k0; k < k1; ++k) {
+            const int rc = c->prec == FR_FP64
+                               ? L_sponge<double>(c, static_cast<double*>(c->u0), nullptr, nullptr, nullptr, k)
+                               : L_sponge<float>(c, static_cast<float*>(c->u0), nullptr, nullptr, nullptr, k);
+            CKL(rc, "sponge kernel");
+        }
+    }
+    c->traces_valid = false;
     invalidate_graph(c);
     CK(cudaDeviceSynchronize());
     return FR_OK;

@@ -99,6 +99,17 @@ struct Launch {
     int threads;      // 32 * epb
 };
 
+// Variable polynomial order (sponge zones): the n listed elements keep their
+// solution in the tensor-product space of degree cap[j] < p; pm[q] holds the
+// 1D L2 projection onto degree q on the GL points, pm[q][i*MAXNP + j].
+template <typename Real>
+struct Sponge {
+    int n = 0;
+    const int32_t* elem = nullptr;
+    const int32_t* cap = nullptr;
+    Real pm[MAXNP][MAXNP * MAXNP];
+};
+
 }  // namespace frk
 
 // Host-side launchers implemented per precision and dimension.
@@ -134,6 +145,12 @@ int sample(int P, const Real* u, const int64_t* pe, const Real* pw, int npts, co
 template <typename Real, int DIM>
 int integrals(int P, const Real* u, int64_t e_first, int64_t ne, const frk::Ops<Real>& op,
               const frk::Geo<Real>& g, double* partial, int nblocks, void* stream);
+
+// project a (and b if not null) of the sponge elements; traces of the
+// projected a into uf_out when not null
+template <typename Real, int DIM>
+int sponge(int P, const frk::Sponge<Real>& sp, Real* a, Real* b, Real* uf_out, const frk::Ops<Real>& op,
+           void* stream);
 
 // energy source share of one stage (Src above) for the source elements
 template <typename Real, int DIM>

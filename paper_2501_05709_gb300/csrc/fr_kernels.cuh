@@ -1210,6 +1210,62 @@ __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __gr
         }
 }
 
+// Variable polynomial order (Section 3.1, sponge zones), after the residual
+// and source kernels of a stage, warp per listed element.  The tensor-product
+// projection onto degree q is the 1D projection pm[q] along each direction in
+// turn; each line of a direction is read and rewritten by one task, so the
+// passes work in place on the staged element.  Array a is projected (its
+// traces written to uf_out when given), then b.  The stage update is linear
+// in R and the stage's inputs already lie in the space, so projecting the
+// stage outputs equals projecting R first.
+template <int DIM, int P, typename Real>
+__global__ void k_sponge(const __grid_constant__ Sponge<Real> sp, Real* __restrict__ a, Real* __restrict__ b,
+                         Real* __restrict__ uf_out, const __grid_constant__ Ops<Real> op) {
+    using Z = Sz<DIM, P>;
+    constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV, NP = P + 1;
+    constexpr int NL = NV * NFP, NLI = (NL + 31) / 32;
+    using VL = Vol<DIM, P, Real>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (j >= sp.n) return;
+    const int64_t e = sp.elem[j];
+    const int q = sp.cap[j];
+    Real pq[NP][NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pq[i][k] = sp.pm[q][i * MAXNP + k];
+    Real* s = reinterpret_cast<Real*>(smem) + warp * NV * NSP;
+    for (int arr = 0; arr < 2; ++arr) {
+        Real* x = arr == 0 ? a : b;
+        if (!x) break;
+        Real* xe = x + e * NV * NSP;
+        warp_stage_vol<DIM, P>(s, xe, lane);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+#pragma unroll 1
+        for (int d = 0; d < DIM; ++d) {
+            for (int t = lane; t < NL; t += 32) {
+                Real l[NP], r[NP];
+                vload_line<DIM, P>(s, t / NFP, d, t % NFP, l);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    r[i] = Real(0);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) r[i] += pq[i][k] * l[k];
+                }
+                vstore_line<DIM, P>(s, t / NFP, d, t % NFP, r);
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < NV * NSP; k += 32) xe[k] = s[VL::pt(k / NSP, k % NSP)];
+        if (arr == 0 && uf_out) warp_write_traces<DIM, P>(s, uf_out + e * NF * NV * NFP, op, lane);
+        __syncwarp();
+    }
+}
+
 // Adaptive time step (Section 3.1: adaptive time stepping): per element
 // lambda_e = max_sp (|V| + c) (p+1)^2 / h_e + max_sp (mu / rho) (p+1)^4 / h_e^2
 // in double, h_e the element length (min over points and directions of

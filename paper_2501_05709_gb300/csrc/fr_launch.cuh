@@ -172,6 +172,20 @@ int source_stage<FR_REAL, FR_DIM>(int P, const frk::Src<FR_REAL>& src, const frk
 }
 
 template <>
+int sponge<FR_REAL, FR_DIM>(int P, const frk::Sponge<FR_REAL>& sp, FR_REAL* a, FR_REAL* b, FR_REAL* uf_out,
+                            const frk::Ops<FR_REAL>& op, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (sp.n <= 0) return 0;
+    const unsigned blocks = unsigned((sp.n + 3) / 4);
+#define C(PP) (frk::k_sponge<FR_DIM, PP, FR_REAL><<<blocks, 128,                                             \
+                   4 * frk::Sz<FR_DIM, PP>::NV * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(sp, a, b, \
+                                                                                              uf_out, op), \
+               int(cudaGetLastError()))
+    FR_DISPATCH(C)
+#undef C
+}
+
+template <>
 int cfl<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* hlen, int64_t E, const int64_t* cand_off,
                          int ncand, const frk::Phys<FR_REAL>& ph, unsigned long long* lam, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);

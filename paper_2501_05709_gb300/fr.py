@@ -89,6 +89,7 @@ _SIGS = {
     "fr_source_time": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "fr_set_adaptive_dt": (C.c_int, [C.c_void_p, C.c_double]),
     "fr_cand_dt": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "fr_set_element_order": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "fr_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fr_launch_count": (C.c_int64, [C.c_void_p]),
@@ -361,6 +362,19 @@ def fr_cand_dt(ctx, cand=0):
     t = C.c_double()
     _check(lib().fr_cand_dt(ctx.handle, int(cand), C.byref(t)))
     return t.value
+
+
+def fr_set_element_order(ctx, order, cand=-1):
+    """Per-element polynomial degree (0..p) of candidate cand (cand = -1: the whole
+    batch); None gives every element of it the context's p again."""
+    if order is None:
+        _check(lib().fr_set_element_order(ctx.handle, int(cand), None))
+        return
+    arr = np.ascontiguousarray(order, dtype=np.int32)
+    _, n = fr_cand_range(ctx, cand)
+    if arr.shape != (n,):
+        raise ValueError(f"order needs {n} entries")
+    _check(lib().fr_set_element_order(ctx.handle, int(cand), _ptr(arr)))
 
 
 def fr_set_tile(ctx, epb):

@@ -110,3 +110,4 @@ def test_new_entry_points_reject_bad_input_on_host(lib):
     assert lib.fr_source_time(None, 0, C.byref(t)) == F.FR_EINVAL
     assert lib.fr_set_adaptive_dt(None, 0.5) == F.FR_EINVAL
     assert lib.fr_cand_dt(None, 0, C.byref(t)) == F.FR_EINVAL
+    assert lib.fr_set_element_order(None, -1, None) == F.FR_EINVAL
