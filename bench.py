@@ -218,6 +218,18 @@ def algorithmic_bytes(E, p, rsz, viscous=True, dim=3, curved=False):
     return {"traces": traces, "visc": visc, "resid": resid}
 
 
+def sponge_bytes(n, p, rsz, dim=3):
+    """Minimum HBM bytes per launch of the reduced-degree projection, stage
+    average: stages 1-3 read and write the stage output and the accumulator,
+    stage 4 the new state; every stage writes the projected state's traces and
+    reads the (element, degree) entry."""
+    np_ = p + 1
+    nsp, nfp, nf, nv = np_ ** dim, np_ ** (dim - 1), 2 * dim, dim + 2
+    u = nv * nsp * rsz
+    tr = nf * nv * nfp * rsz
+    return n * ((3 * 4 * u + 2 * u) / 4.0 + tr + 8)
+
+
 WORKLOADS = {
     "tgv32_p3": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, FR p=3 (2,097,152 DOF), "
                 "Rusanov+BR2, RK4 dt=2.5e-4",
@@ -314,6 +326,13 @@ def gpu_leg(args, rank, world, local_rank):
         F.fr_set_cand_dt(ctx, k, d)
     if args.workload.startswith("monopole"):
         F.fr_set_source(ctx, 0, C.MONOPOLE_SOURCE, 0.0)
+    orders = None
+    if args.sponge:
+        # far-field sponge of reduced degree on the O-grid candidates
+        if not args.workload.startswith(("naca", "batch")):
+            raise SystemExit("--sponge needs an O-grid workload (naca100k_p3, batch12_p3)")
+        orders = np.concatenate([W.sponge_orders(n, ctx.order) for n, _ in meshes])
+        F.fr_set_element_order(ctx, orders)
     viscous = bool(ctx_viscous(opts(prec)))
     p = ctx.order
     u0 = state_of(ctx)
@@ -370,6 +389,11 @@ def gpu_leg(args, rank, world, local_rank):
         return {"avg_ms": avg, "launches": int(kn[i]), "gbs": (ab[key] / (avg / 1e3) / 1e9) if avg > 0 else None}
 
     kernels = {"traces": kstat(0, "traces"), "visc_face": kstat(1, "visc"), "residual_rk": kstat(2, "resid")}
+    if orders is not None:
+        nred = int((orders < p).sum())
+        ab["sponge"] = sponge_bytes(nred, p, rsz)
+        kernels["sponge_projection"] = dict(kstat(5, "sponge"), elements=nred,
+                                            degrees=np.bincount(orders, minlength=p + 1).tolist())
     u32 = F.fr_state_get(ctx)
     steps_done = args.warmup + 2 * args.steps
 
@@ -402,6 +426,8 @@ def gpu_leg(args, rank, world, local_rank):
             F.fr_set_cand_dt(c64, k, d)
         if args.workload.startswith("monopole"):
             F.fr_set_source(c64, 0, C.MONOPOLE_SOURCE, 0.0)
+        if orders is not None:
+            F.fr_set_element_order(c64, orders)
         F.fr_state_set(c64, u0)
         for k, srf in enumerate(surfaces):
             F.fwh_register(c64, k, srf, cap, 1)
@@ -525,6 +551,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwh", action="store_true", help="skip the FW-H/PSD post-processing timing")
     ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
+    ap.add_argument("--sponge", action="store_true",
+                    help="O-grid workloads: degree p near the body down to 0 at the far field (4c/6c/8c)")
     ap.add_argument("--workload", default="tgv32_p3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the timed path (fp32 also times fp64 beside it)")
@@ -573,6 +601,8 @@ def main():
                 cb_all = run_oracle_all_cores(min_seconds=10.0)
             except Exception as e:
                 cb_all = {"value": None, "error": str(e)[-300:]}
+        if args.sponge:
+            config["sponge"] = "element degree p inside 4c of (0.5, 0), then p-1, p-2, p-3 (>= 0) past 4c, 6c, 8c"
         config["autotuned_elements_per_block"] = r["tile_epb"]
         config["elements"] = r["elements"]
         config["dof_per_variable"] = r["dof"]

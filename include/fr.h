@@ -328,10 +328,10 @@ int64_t fr_launch_count(const fr_ctx* ctx);
 
 /* Measurement aid: runs nsteps RK4 steps without a graph on stream with a
  * CUDA event around every launch and returns the summed device time (ms)
- * per kernel kind in ms_out[0..3] = traces, viscous faces, residual+RK,
- * forces/sampling, and their launch counts in n_out[0..3].  Advances the
- * state exactly like fr_rk_step. */
-int fr_profile_step(fr_ctx* ctx, int nsteps, void* stream, double ms_out[4], int64_t n_out[4]);
+ * per kernel kind in ms_out[0..5] = traces, viscous faces, residual+RK,
+ * forces/sampling, energy source, reduced-degree projection, and their launch
+ * counts in n_out[0..5].  Advances the state exactly like fr_rk_step. */
+int fr_profile_step(fr_ctx* ctx, int nsteps, void* stream, double ms_out[6], int64_t n_out[6]);
 
 #ifdef __cplusplus
 }

@@ -305,7 +305,7 @@ int L_sample(fr_ctx* c, Surface& sf, cudaStream_t s) {
                                               static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.every, s);
 }
 
-// Optional per-launch event pairs for fr_profile_step: kind 0..3.
+// Optional per-launch event pairs for fr_profile_step: kind 0..5.
 struct Prof {
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind;
@@ -400,11 +400,15 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
         if (c->src_nentry > 0) {
+            if (pr) pr->mark_begin(4);
             rc = L_source<Real>(c, src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5), st, s);
+            if (pr) pr->mark_end();
             CKL(rc, "source kernel");
         }
         if (c->sp_n > 0) {
+            if (pr) pr->mark_begin(5);
             rc = stage == 4 ? L_sponge<Real>(c, u0, nullptr, uf_out, s) : L_sponge<Real>(c, us, acc, uf_out, s);
+            if (pr) pr->mark_end();
             CKL(rc, "sponge kernel");
         }
     }
@@ -1673,11 +1677,11 @@ extern "C" int fr_probe_fp64_peak(double* gflops, void* stream) {
     return FR_OK;
 }
 
-extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_out[4], int64_t n_out[4]) {
+extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_out[6], int64_t n_out[6]) {
     if (!c || nsteps < 0 || !ms_out || !n_out) return fail(FR_EINVAL, "bad argument");
     Prof pr;
     pr.s = static_cast<cudaStream_t>(stream);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 6; ++k) {
         ms_out[k] = 0.0;
         n_out[k] = 0;
     }

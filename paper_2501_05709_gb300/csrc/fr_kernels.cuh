@@ -1214,16 +1214,17 @@ __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __gr
 // and source kernels of a stage, warp per listed element.  The tensor-product
 // projection onto degree q is the 1D projection pm[q] along each direction in
 // turn; each line of a direction is read and rewritten by one task, so the
-// passes work in place on the staged element.  Array a is projected (its
-// traces written to uf_out when given), then b.  The stage update is linear
-// in R and the stage's inputs already lie in the space, so projecting the
-// stage outputs equals projecting R first.
+// passes work in place on the staged element.  Arrays a and b (when given) are
+// staged together, projected, and written back; the traces of the projected a
+// go to uf_out when given.  The stage update is linear in R and the stage's
+// inputs already lie in the space, so projecting the stage outputs equals
+// projecting R first.
 template <int DIM, int P, typename Real>
 __global__ void k_sponge(const __grid_constant__ Sponge<Real> sp, Real* __restrict__ a, Real* __restrict__ b,
                          Real* __restrict__ uf_out, const __grid_constant__ Ops<Real> op) {
     using Z = Sz<DIM, P>;
     constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV, NP = P + 1;
-    constexpr int NL = NV * NFP, NLI = (NL + 31) / 32;
+    constexpr int NL = NV * NFP;
     using VL = Vol<DIM, P, Real>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1236,15 +1237,17 @@ __global__ void k_sponge(const __grid_constant__ Sponge<Real> sp, Real* __restri
     for (int i = 0; i < NP; ++i)
 #pragma unroll
         for (int k = 0; k < NP; ++k) pq[i][k] = sp.pm[q][i * MAXNP + k];
-    Real* s = reinterpret_cast<Real*>(smem) + warp * NV * NSP;
-    for (int arr = 0; arr < 2; ++arr) {
-        Real* x = arr == 0 ? a : b;
-        if (!x) break;
-        Real* xe = x + e * NV * NSP;
-        warp_stage_vol<DIM, P>(s, xe, lane);
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncwarp();
+    Real* sa = reinterpret_cast<Real*>(smem) + warp * 2 * NV * NSP;
+    Real* sb = sa + NV * NSP;
+    const int narr = b ? 2 : 1;
+    warp_stage_vol<DIM, P>(sa, a + e * NV * NSP, lane);
+    if (b) warp_stage_vol<DIM, P>(sb, b + e * NV * NSP, lane);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+#pragma unroll 1
+    for (int arr = 0; arr < narr; ++arr) {
+        Real* s = arr == 0 ? sa : sb;
 #pragma unroll 1
         for (int d = 0; d < DIM; ++d) {
             for (int t = lane; t < NL; t += 32) {
@@ -1260,10 +1263,14 @@ __global__ void k_sponge(const __grid_constant__ Sponge<Real> sp, Real* __restri
             }
             __syncwarp();
         }
-        for (int k = lane; k < NV * NSP; k += 32) xe[k] = s[VL::pt(k / NSP, k % NSP)];
-        if (arr == 0 && uf_out) warp_write_traces<DIM, P>(s, uf_out + e * NF * NV * NFP, op, lane);
-        __syncwarp();
     }
+    Real* ae = a + e * NV * NSP;
+    for (int k = lane; k < NV * NSP; k += 32) ae[k] = sa[VL::pt(k / NSP, k % NSP)];
+    if (b) {
+        Real* be = b + e * NV * NSP;
+        for (int k = lane; k < NV * NSP; k += 32) be[k] = sb[VL::pt(k / NSP, k % NSP)];
+    }
+    if (uf_out) warp_write_traces<DIM, P>(sa, uf_out + e * NF * NV * NFP, op, lane);
 }
 
 // Adaptive time step (Section 3.1: adaptive time stepping): per element

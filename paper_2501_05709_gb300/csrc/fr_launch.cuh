@@ -178,7 +178,7 @@ int sponge<FR_REAL, FR_DIM>(int P, const frk::Sponge<FR_REAL>& sp, FR_REAL* a, F
     if (sp.n <= 0) return 0;
     const unsigned blocks = unsigned((sp.n + 3) / 4);
 #define C(PP) (frk::k_sponge<FR_DIM, PP, FR_REAL><<<blocks, 128,                                             \
-                   4 * frk::Sz<FR_DIM, PP>::NV * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(sp, a, b, \
+                   8 * frk::Sz<FR_DIM, PP>::NV * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(sp, a, b, \
                                                                                               uf_out, op), \
                int(cudaGetLastError()))
     FR_DISPATCH(C)

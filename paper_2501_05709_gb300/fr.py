@@ -399,8 +399,9 @@ def fr_probe_fp64_peak(stream=None):
 
 
 def fr_profile_step(ctx, nsteps, stream=None):
-    """(ms [4], launches [4]) per kernel kind: traces, viscous faces, residual+RK, forces/sampling."""
-    ms = np.zeros(4)
-    n = np.zeros(4, dtype=np.int64)
+    """(ms [6], launches [6]) per kernel kind: traces, viscous faces, residual+RK, forces/sampling,
+    energy source, reduced-degree projection."""
+    ms = np.zeros(6)
+    n = np.zeros(6, dtype=np.int64)
     _check(lib().fr_profile_step(ctx.handle, int(nsteps), _stream(stream), _ptr(ms), _ptr(n)))
     return ms, n

@@ -266,6 +266,20 @@ def ogrid_mesh(n_theta, n_r, n_z, span, r_outer=10.0, first_cell=2e-3, body="nac
 # closed-form flow fields (conserved variables [rho, rho*V, rho*E])
 # --------------------------------------------------------------------------
 
+def sponge_orders(nodes, p, center=(0.5, 0.0), radii=(4.0, 6.0, 8.0)):
+    """Per-element polynomial degree for the far-field sponge of Section 3.1:
+    degree p inside radii[0] of ``center`` (element centroid in the x-y plane),
+    then one degree less past each further radius, never below 0.  With the
+    defaults and p = 3 on a 10c O-grid: p3 near the body, p2 from 4c, p1 from
+    6c, p0 from 8c out to the far-field boundary."""
+    X = np.asarray(nodes, float)
+    r = np.hypot(X[:, :, 0].mean(axis=1) - center[0], X[:, :, 1].mean(axis=1) - center[1])
+    drop = np.zeros(len(X), np.int32)
+    for rr in radii:
+        drop += (r >= rr).astype(np.int32)
+    return np.maximum(p - drop, 0).astype(np.int32)
+
+
 def primitive_to_conserved(rho, vel, p, gamma=GAMMA):
     vel = np.asarray(vel)
     ke = 0.5 * rho * np.sum(vel * vel, axis=0)
