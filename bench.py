@@ -301,6 +301,23 @@ def build_workload(name):
     return meshes, opts, state, [surf] * len(meshes), True, dts
 
 
+def max_over_ranks_of(x, world, device):
+    """The largest x over the ranks of the default process group (the job's
+    time is its slowest replica's); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, seconds_max, world):
+    """Whole-job rate of N independent replicas: every rank's units over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def ctx_viscous(o):
     return int(o.viscous)
 
@@ -356,11 +373,7 @@ def gpu_leg(args, rank, world, local_rank):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if world > 1:
-            t = torch.tensor([x], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return max_over_ranks_of(x, world, "cuda")
 
     clocks = Clocks(local_rank) if rank == 0 else None
     time.sleep(0.3)
@@ -376,7 +389,7 @@ def gpu_leg(args, rank, world, local_rank):
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     launches = F.fr_launch_count(ctx) - n0
     ck = clocks.stop() if clocks else None
-    value = world * dof * 4 * args.steps / (ms / 1e3)
+    value = replica_throughput(dof * 4 * args.steps, ms / 1e3, world)
 
     # per-kernel durations of the same steps, events around each launch
     kms, kn = F.fr_profile_step(ctx, args.steps, sh)
@@ -414,7 +427,7 @@ def gpu_leg(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * dof * 4 * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": replica_throughput(dof * 4 * args.steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(8 * 6 * min(1024, (dof + 255) // 256))}
     ctx.close()
 
@@ -454,7 +467,7 @@ def gpu_leg(args, rank, world, local_rank):
         dev = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
         ke = F.fr_integrals(c64)[-1]
         c64.close()
-        fp64 = {"value": world * dof * 4 * args.steps / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / args.steps,
+        fp64 = {"value": replica_throughput(dof * 4 * args.steps, ms64 / 1e3, world), "unit": UNIT, "ms_per_step": ms64 / args.steps,
                 "fp32_state_rel_l2_vs_fp64": dev, "steps_compared": steps_done, "ke_fp64": ke}
         # FP64 kernels are bound by the FP64 pipe: executed FP64 flops per
         # launch (ncu: 2 DFMA + DADD + DMUL, stage average) against the DFMA
