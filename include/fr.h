@@ -104,7 +104,9 @@ typedef struct {
 } fr_options;
 
 /* Context sizes: out[0]=dim, [1]=order p, [2]=nvar, [3]=Nsp, [4]=total
- * elements E, [5]=ncand, [6]=precision, [7]=1 if every element is affine. */
+ * elements E, [5]=ncand, [6]=precision, [7]=metric path: 0 per-point metrics
+ * (some element is curved), 1 every element affine (one metric set per
+ * element), 2 every element affine and axis-aligned (diagonal metrics). */
 int fr_ctx_dims(const fr_ctx* ctx, int64_t out[8]);
 
 /* fr_mesh_load (Section 3.1 mesh of curved hexahedra; FR set-up of Section 1):

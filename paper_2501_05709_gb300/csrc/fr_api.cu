@@ -49,7 +49,7 @@ struct Surface {
 
 struct fr_ctx {
     int dim = 0, p = 0, np = 0, nsp = 0, nfp = 0, nf = 0, nv = 0;
-    int ncand = 0, prec = 0, visc = 0, kind = 0, affine = 0;
+    int ncand = 0, prec = 0, visc = 0, kind = 0, affine = 0, diag = 0;
     int64_t E = 0;
     fr_options opt{};
     std::vector<int64_t> cand_off;
@@ -153,6 +153,7 @@ frk::Geo<Real> geo_of(const fr_ctx* c) {
     g.sJ_sp = c->sJ_sp;
     g.sN_f = c->sN_f;
     g.sN_fp = c->sN_fp;
+    g.diag = c->diag;
     return g;
 }
 
@@ -546,7 +547,7 @@ extern "C" int fr_ctx_dims(const fr_ctx* c, int64_t out[8]) {
     out[4] = c->E;
     out[5] = c->ncand;
     out[6] = c->prec;
-    out[7] = c->affine;
+    out[7] = c->affine + c->diag;
     return FR_OK;
 }
 
@@ -754,6 +755,24 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
             for (int f = 0; f < nf; ++f)
                 for (int i = 0; i < dim; ++i) N1[(e * nf + f) * dim + i] = Nsh[((e * nf + f) * nfp) * dim + i];
         }
+        // axis-aligned elements: when every off-diagonal S entry of every
+        // element is round-off (at most 1e-13 of its row's largest entry),
+        // those entries become exact zeros and the kernels skip them
+        bool diag = true;
+        for (int64_t e = 0; e < E && diag; ++e)
+            for (int d = 0; d < dim && diag; ++d) {
+                const double* row = &S1[e * dim * dim + d * dim];
+                double mx = 0.0;
+                for (int i = 0; i < dim; ++i) mx = std::max(mx, std::fabs(row[i]));
+                for (int i = 0; i < dim; ++i)
+                    if (i != d && std::fabs(row[i]) > 1e-13 * mx) diag = false;
+            }
+        if (diag)
+            for (int64_t e = 0; e < E; ++e)
+                for (int d = 0; d < dim; ++d)
+                    for (int i = 0; i < dim; ++i)
+                        if (i != d) S1[e * dim * dim + d * dim + i] = 0.0;
+        c->diag = diag ? 1 : 0;
         // the larger (element, face) side takes the exact negative of the
         // smaller side's constant normal, so common fluxes stay equal and opposite
         for (int64_t e = 0; e < E; ++e)

@@ -52,6 +52,9 @@ struct Geo {
     int64_t sS_e, sS_k, sS_sp;
     int64_t sJ_e, sJ_sp;
     int64_t sN_f, sN_fp;
+    // 1: every element is affine with a diagonal S (axis-aligned boxes; the
+    // off-diagonal entries are exact zeros), so S^T q and S F take one term
+    int diag;
 };
 
 // RK4 stage control for the fused residual/update kernel.

@@ -632,8 +632,10 @@ __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int6
 
 // Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
 // boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
-// an adiabatic wall) is written instead.
-template <int DIM, int P, typename Real>
+// an adiabatic wall) is written instead.  MP is the mesh's metric path, fixed
+// at compile time: 0 per-point metrics (curved), 1 one metric set per element
+// (affine), 2 affine with diagonal S (axis-aligned).
+template <int DIM, int P, typename Real, int MP>
 __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
                             int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
                             const __grid_constant__ Geo<Real> g) {
@@ -649,7 +651,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     if (e >= E) return;
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
-    const bool curved = g.sS_sp != 0;               // per-point metrics, staged after region D
+    constexpr bool curved = MP == 0;                // per-point metrics, staged after region D
+    constexpr bool diag = MP == 2;                  // affine, diagonal S
     Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc);
     Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
     Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
@@ -750,10 +753,33 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             load_S<DIM>(g, e, 0, S);
             iJ = g.iJ[e * g.sJ_e];
         }
+        if constexpr (diag) {
+            // axis-aligned: the off-diagonal terms are exact zeros
+#pragma unroll
+            for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sg[VL::pt(i * NV + v, sp)] = S[i * DIM + i] * q[i][v] * iJ;
+            continue;
+        }
+        if constexpr (sizeof(Real) == 4) {
+            // pairs of variables as packed FP32x2 (the same order of operations)
+#pragma unroll
+            for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                for (int v = 0; v + 1 < NV; v += 2) {
+                    float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+                        a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]), make_float2(q[d][v], q[d][v + 1]), a);
+                    a = __fmul2_rn(a, make_float2(iJ, iJ));
+                    sg[VL::pt(i * NV + v, sp)] = a.x;
+                    sg[VL::pt(i * NV + v + 1, sp)] = a.y;
+                }
+        }
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
+            for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
                 Real acc = Real(0);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
@@ -841,8 +867,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 
 // Sweep C: common fluxes, corrected gradient, flux divergence with the FR
 // correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
-// stages) the traces of the updated state written for the next stage.
-template <int DIM, int P, typename Real>
+// stages) the traces of the updated state written for the next stage.  MP as
+// for k_visc_face.
+template <int DIM, int P, typename Real, int MP>
 __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
                            const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
                            const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
@@ -860,7 +887,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     if (e >= E) return;
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
-    const bool curved = g.sS_sp != 0;               // per-point metrics, staged in region E
+    constexpr bool curved = MP == 0;                // per-point metrics, staged in region E
+    constexpr bool diag = MP == 2;                  // affine, diagonal S
     Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::resid_c : SM::resid);
     Real* sj = su + SM::rB;              // jumps u_c - u_f      [f][v][fp]
     Real* sd = sj;                       // divergence [v][sp], after the gradient
@@ -1034,15 +1062,37 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
         if (ph.viscous) {
             const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
             Real G[NV][DIM];
+            if constexpr (diag) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+                for (int v = 0; v < NV; ++v)
 #pragma unroll
-                for (int i = 0; i < DIM; ++i) {
-                    Real acc = Real(0);
+                    for (int i = 0; i < DIM; ++i) G[v][i] = S[i * DIM + i] * sF[VL::pt(i * NV + v, sp)] * iJ;
+            } else {
+                if constexpr (sizeof(Real) == 4) {
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * sF[VL::pt(d * NV + v, sp)];
-                    G[v][i] = acc * iJ;
+                    for (int v = 0; v + 1 < NV; v += 2)
+#pragma unroll
+                        for (int i = 0; i < DIM; ++i) {
+                            float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                            for (int d = 0; d < DIM; ++d)
+                                a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]),
+                                               make_float2(sF[VL::pt(d * NV + v, sp)], sF[VL::pt(d * NV + v + 1, sp)]), a);
+                            a = __fmul2_rn(a, make_float2(iJ, iJ));
+                            G[v][i] = a.x;
+                            G[v + 1][i] = a.y;
+                        }
                 }
+#pragma unroll
+                for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v)
+#pragma unroll
+                    for (int i = 0; i < DIM; ++i) {
+                        Real acc = Real(0);
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * sF[VL::pt(d * NV + v, sp)];
+                        G[v][i] = acc * iJ;
+                    }
+            }
             Real Fv[NV][DIM];
             visc_flux<DIM>(uu, G, ph.mu, ph.kappa, Fv);
 #pragma unroll
@@ -1050,10 +1100,30 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) F[v][i] -= Fv[v][i];
         }
+        if constexpr (diag) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sF[VL::pt(d * NV + v, sp)] = S[d * DIM + d] * F[v][d];
+            continue;
+        }
+        if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                for (int v = 0; v + 1 < NV; v += 2) {
+                    float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int i = 0; i < DIM; ++i)
+                        a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]), make_float2(F[v][i], F[v + 1][i]), a);
+                    sF[VL::pt(d * NV + v, sp)] = a.x;
+                    sF[VL::pt(d * NV + v + 1, sp)] = a.y;
+                }
+        }
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
+            for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
                 Real acc = Real(0);
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];

@@ -35,10 +35,13 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& 
     return int(cudaGetLastError());
 }
 
-template <int P>
+// metric path of the kernels: 0 per-point metrics, 1 affine, 2 affine with diagonal S
+inline int metric_path(const frk::Geo<FR_REAL>& g) { return g.sS_sp != 0 ? 0 : g.diag ? 2 : 1; }
+
+template <int P, int MP>
 int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>& op,
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL>;
+    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP>;
     const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
@@ -48,11 +51,11 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     return int(cudaGetLastError());
 }
 
-template <int P>
+template <int P, int MP>
 int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_residual<FR_DIM, P, FR_REAL>;
+    auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
@@ -87,7 +90,10 @@ int visc_face<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, FR_RE
                                const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph,
                                const frk::Geo<FR_REAL>& g, frk::Launch lc, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-#define C(PP) visc_p<PP>(u, uf, fvn, E, op, ph, g, lc, s)
+    const int mp = metric_path(g);
+#define C(PP) (mp == 0 ? visc_p<PP, 0>(u, uf, fvn, E, op, ph, g, lc, s)   \
+               : mp == 1 ? visc_p<PP, 1>(u, uf, fvn, E, op, ph, g, lc, s) \
+                         : visc_p<PP, 2>(u, uf, fvn, E, op, ph, g, lc, s))
     FR_DISPATCH(C)
 #undef C
 }
@@ -98,7 +104,10 @@ int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const 
                               const frk::Geo<FR_REAL>& g, const frk::Stage<FR_REAL>& st, frk::Launch lc,
                               void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-#define C(PP) resid_p<PP>(u, uf, fvn, E, op, ph, g, st, lc, s)
+    const int mp = metric_path(g);
+#define C(PP) (mp == 0 ? resid_p<PP, 0>(u, uf, fvn, E, op, ph, g, st, lc, s)   \
+               : mp == 1 ? resid_p<PP, 1>(u, uf, fvn, E, op, ph, g, st, lc, s) \
+                         : resid_p<PP, 2>(u, uf, fvn, E, op, ph, g, st, lc, s))
     FR_DISPATCH(C)
 #undef C
 }

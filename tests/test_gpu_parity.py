@@ -43,20 +43,20 @@ def test_residual_fp64(name):
     assert relerr(R, R_or) <= fp64_tol(s.residual, u)
 
 
-AFFINE = {"vortex2d_p2", "tgv3d_p3", "single_element"}
+METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1}
 
 
 @pytest.mark.parametrize("name", CASES)
 def test_affine_detection(name):
-    """Straight-sided axis-aligned meshes take the per-element metric path
-    (round-off in analytically zero metric components is not variation);
-    curved meshes keep per-point metrics."""
+    """Straight-sided meshes take the per-element metric path (round-off in
+    analytically zero metric components is not variation), axis-aligned ones
+    the diagonal-metric path; curved meshes keep per-point metrics."""
     c = make_case(name)
     with _load(c) as ctx:
-        assert ctx.affine == (1 if name in AFFINE else 0)
+        assert ctx.affine == METRIC_PATH.get(name, 0)
 
 
-@pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2"])
+@pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2", "rot3d_p3"])
 def test_rk4_steps_fp64(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
@@ -95,7 +95,7 @@ def test_graph_replay_matches_direct_stepping():
     assert np.array_equal(fa, fb)
 
 
-@pytest.mark.parametrize("name", ["tgv3d_p3", "ns3d_curved_p3"])
+@pytest.mark.parametrize("name", ["tgv3d_p3", "ns3d_curved_p3", "rot3d_p3"])
 def test_conservation_on_gpu(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
@@ -183,7 +183,7 @@ def test_fwh_integrate_matches_oracle():
 def test_fp32_residual_error_is_bounded():
     # stated FP32 bound: relative L2 of the residual against the FP64 oracle
     from paper_2501_05709_gb300 import fr as F
-    for name, tol in (("ns3d_curved_p3", 1e-5), ("ns3d_ogrid_p3", 1e-4), ("tgv3d_p3", 1e-3)):
+    for name, tol in (("ns3d_curved_p3", 1e-5), ("ns3d_ogrid_p3", 1e-4), ("tgv3d_p3", 1e-3), ("rot3d_p3", 1e-5)):
         c = make_case(name)
         m, s = oracle_for(c)
         u = c["state"](m.xsp)
@@ -195,6 +195,25 @@ def test_fp32_residual_error_is_bounded():
             torch.cuda.synchronize()
             R = Rd.double().cpu().numpy()
         assert relerr(R, R_or) <= tol, name
+
+
+def test_diagonal_metric_path_matches_the_full_one():
+    # the axis-aligned path (metric path 2) skips the exact-zero metric terms
+    # and agrees with the oracle in both precisions; the turned box of
+    # rot3d_p3 covers the full affine path (1) in the tests above
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("tgv3d_p3")
+    m, s = oracle_for(c)
+    u = c["state"](m.xsp)
+    for prec, tol in ((0, fp64_tol(s.residual, u)), (1, 1e-3)):
+        with _load(c, precision=prec) as ctx:
+            assert ctx.affine == 2
+            dt = torch.float64 if prec == 0 else torch.float32
+            ud = torch.tensor(u, device="cuda", dtype=dt)
+            Rd = torch.empty_like(ud)
+            F.fr_residual(ctx, ud, Rd)
+            torch.cuda.synchronize()
+            assert relerr(Rd.double().cpu().numpy(), s.residual(u)) <= tol
 
 
 def test_autotune_keeps_results():
