@@ -868,8 +868,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 // Sweep C: common fluxes, corrected gradient, flux divergence with the FR
 // correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
 // stages) the traces of the updated state written for the next stage.  MP as
-// for k_visc_face.
-template <int DIM, int P, typename Real, int MP>
+// for k_visc_face; VISC: Navier-Stokes (BR2 viscous terms) or Euler.
+template <int DIM, int P, typename Real, int MP, bool VISC>
 __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
                            const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
                            const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
@@ -915,10 +915,10 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     for (int f = 0; f < NF; ++f)
         if (codes[f] >= 0) {
             warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
-            if (ph.viscous)
+            if constexpr (VISC)
                 warp_stage<NV * NFP, VS>(sm + f * NV * NFP, fvn + int64_t(codes[f] >> 3) * NV * NFP, lane);
         }
-    if (ph.viscous) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane);
+    if constexpr (VISC) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane);
     cp_async_commit();
     // face normals of this lane's face points, and the RK stage arrays (needed
     // only at the end): issue their loads now
@@ -981,7 +981,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             }
             Real Fc[NV];
             rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
-            if (ph.viscous) {
+            if constexpr (VISC) {
                 const Real* own = so + f * NV * NFP + fp;
                 if (code >= 0) {
                     const Real* nb = sm + f * NV * NFP + fpn;
@@ -1010,7 +1010,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     }
     // C1 (viscous): corrected reference gradient along lines,
     // q_d = D_d u + nsign h_f (u_c - u_f) for the two faces normal to d
-    if (ph.viscous) {
+    if constexpr (VISC) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
 #pragma unroll 1
@@ -1059,7 +1059,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             for (int i = 0; i < DIM; ++i) F[1 + i][j] = uu[1 + i] * vj + (i == j ? p : Real(0));
             F[NV - 1][j] = (uu[NV - 1] + p) * vj;
         }
-        if (ph.viscous) {
+        if constexpr (VISC) {
             const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
             Real G[NV][DIM];
             if constexpr (diag) {

@@ -51,11 +51,11 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     return int(cudaGetLastError());
 }
 
-template <int P, int MP>
+template <int P, int MP, bool VISC>
 int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP>;
+    auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP, VISC>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
@@ -105,11 +105,13 @@ int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const 
                               void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mp = metric_path(g);
-#define C(PP) (mp == 0 ? resid_p<PP, 0>(u, uf, fvn, E, op, ph, g, st, lc, s)   \
-               : mp == 1 ? resid_p<PP, 1>(u, uf, fvn, E, op, ph, g, st, lc, s) \
-                         : resid_p<PP, 2>(u, uf, fvn, E, op, ph, g, st, lc, s))
+#define R(PP, V) (mp == 0 ? resid_p<PP, 0, V>(u, uf, fvn, E, op, ph, g, st, lc, s)   \
+                  : mp == 1 ? resid_p<PP, 1, V>(u, uf, fvn, E, op, ph, g, st, lc, s) \
+                            : resid_p<PP, 2, V>(u, uf, fvn, E, op, ph, g, st, lc, s))
+#define C(PP) (ph.viscous ? R(PP, true) : R(PP, false))
     FR_DISPATCH(C)
 #undef C
+#undef R
 }
 
 template <>
