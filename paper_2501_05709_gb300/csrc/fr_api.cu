@@ -49,7 +49,7 @@ struct Surface {
 
 struct fr_ctx {
     int dim = 0, p = 0, np = 0, nsp = 0, nfp = 0, nf = 0, nv = 0;
-    int ncand = 0, prec = 0, visc = 0, kind = 0, affine = 0, diag = 0;
+    int ncand = 0, prec = 0, visc = 0, kind = 0, affine = 0, diag = 0, bnd = 1;
     int64_t E = 0;
     fr_options opt{};
     std::vector<int64_t> cand_off;
@@ -154,6 +154,7 @@ frk::Geo<Real> geo_of(const fr_ctx* c) {
     g.sN_f = c->sN_f;
     g.sN_fp = c->sN_fp;
     g.diag = c->diag;
+    g.bnd = c->bnd;
     return g;
 }
 
@@ -805,6 +806,9 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
             return rc;
         }
     }
+    c->bnd = 0;
+    for (const int32_t code : nbr)
+        if (code < 0) c->bnd = 1;
     if ((rc = upload(reinterpret_cast<void**>(&c->nbr), nbr))) {
         release(c);
         return rc;

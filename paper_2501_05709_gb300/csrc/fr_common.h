@@ -55,6 +55,8 @@ struct Geo {
     // 1: every element is affine with a diagonal S (axis-aligned boxes; the
     // off-diagonal entries are exact zeros), so S^T q and S F take one term
     int diag;
+    // 1: some element face lies on a boundary (0: fully periodic mesh)
+    int bnd;
 };
 
 // RK4 stage control for the fused residual/update kernel.

@@ -634,8 +634,9 @@ __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int6
 // boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
 // an adiabatic wall) is written instead.  MP is the mesh's metric path, fixed
 // at compile time: 0 per-point metrics (curved), 1 one metric set per element
-// (affine), 2 affine with diagonal S (axis-aligned).
-template <int DIM, int P, typename Real, int MP>
+// (affine), 2 affine with diagonal S (axis-aligned); BND false: the mesh has
+// no boundary faces (fully periodic), so the boundary-state code is left out.
+template <int DIM, int P, typename Real, int MP, bool BND>
 __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
                             int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
                             const __grid_constant__ Geo<Real> g) {
@@ -701,7 +702,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
             for (int v = 0; v < NV; ++v) uL[v] = sl[(f * NV + v) * NFP + fp];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
-            if (code >= 0) {
+            if (!BND || code >= 0) {
                 const Real* un = sn + f * NV * NFP;
                 const int fpn = omap<DIM, NP>(code & 7, fp);
 #pragma unroll
@@ -845,7 +846,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             Real Fv[NV][DIM];
-            if (code >= 0) {
+            if (!BND || code >= 0) {
                 visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
             } else {
                 Real ug[NV], ub[NV];
@@ -867,9 +868,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 
 // Sweep C: common fluxes, corrected gradient, flux divergence with the FR
 // correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
-// stages) the traces of the updated state written for the next stage.  MP as
-// for k_visc_face; VISC: Navier-Stokes (BR2 viscous terms) or Euler.
-template <int DIM, int P, typename Real, int MP, bool VISC>
+// stages) the traces of the updated state written for the next stage.  MP and
+// BND as for k_visc_face; VISC: Navier-Stokes (BR2 viscous terms) or Euler.
+template <int DIM, int P, typename Real, int MP, bool VISC, bool BND>
 __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
                            const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
                            const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
@@ -968,7 +969,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
             int fpn = 0;
-            if (code >= 0) {
+            if (!BND || code >= 0) {
                 fpn = omap<DIM, NP>(code & 7, fp);
                 const Real* un = sn + f * NV * NFP;
 #pragma unroll
@@ -983,7 +984,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
             if constexpr (VISC) {
                 const Real* own = so + f * NV * NFP + fp;
-                if (code >= 0) {
+                if (!BND || code >= 0) {
                     const Real* nb = sm + f * NV * NFP + fpn;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) Fc[v] -= Real(0.5) * (own[v * NFP] - nb[v * NFP]);

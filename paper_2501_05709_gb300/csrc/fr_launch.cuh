@@ -38,10 +38,10 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& 
 // metric path of the kernels: 0 per-point metrics, 1 affine, 2 affine with diagonal S
 inline int metric_path(const frk::Geo<FR_REAL>& g) { return g.sS_sp != 0 ? 0 : g.diag ? 2 : 1; }
 
-template <int P, int MP>
+template <int P, int MP, bool BND>
 int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>& op,
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP>;
+    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP, BND>;
     const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
@@ -51,11 +51,11 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     return int(cudaGetLastError());
 }
 
-template <int P, int MP, bool VISC>
+template <int P, int MP, bool VISC, bool BND>
 int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Ops<FR_REAL>& op, const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP, VISC>;
+    auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP, VISC, BND>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
     static bool done = false;
     cudaError_t e = prep(k, sm, done);
@@ -91,11 +91,13 @@ int visc_face<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, FR_RE
                                const frk::Geo<FR_REAL>& g, frk::Launch lc, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mp = metric_path(g);
-#define C(PP) (mp == 0 ? visc_p<PP, 0>(u, uf, fvn, E, op, ph, g, lc, s)   \
-               : mp == 1 ? visc_p<PP, 1>(u, uf, fvn, E, op, ph, g, lc, s) \
-                         : visc_p<PP, 2>(u, uf, fvn, E, op, ph, g, lc, s))
+    // curved meshes always take the boundary-aware kernels
+#define V(PP, M) (g.bnd ? visc_p<PP, M, true>(u, uf, fvn, E, op, ph, g, lc, s) \
+                        : visc_p<PP, M, false>(u, uf, fvn, E, op, ph, g, lc, s))
+#define C(PP) (mp == 0 ? visc_p<PP, 0, true>(u, uf, fvn, E, op, ph, g, lc, s) : mp == 1 ? V(PP, 1) : V(PP, 2))
     FR_DISPATCH(C)
 #undef C
+#undef V
 }
 
 template <>
@@ -105,13 +107,15 @@ int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const 
                               void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mp = metric_path(g);
-#define R(PP, V) (mp == 0 ? resid_p<PP, 0, V>(u, uf, fvn, E, op, ph, g, st, lc, s)   \
-                  : mp == 1 ? resid_p<PP, 1, V>(u, uf, fvn, E, op, ph, g, st, lc, s) \
-                            : resid_p<PP, 2, V>(u, uf, fvn, E, op, ph, g, st, lc, s))
+#define B(PP, M, V) (g.bnd ? resid_p<PP, M, V, true>(u, uf, fvn, E, op, ph, g, st, lc, s) \
+                           : resid_p<PP, M, V, false>(u, uf, fvn, E, op, ph, g, st, lc, s))
+#define R(PP, V) (mp == 0 ? resid_p<PP, 0, V, true>(u, uf, fvn, E, op, ph, g, st, lc, s) \
+                  : mp == 1 ? B(PP, 1, V) : B(PP, 2, V))
 #define C(PP) (ph.viscous ? R(PP, true) : R(PP, false))
     FR_DISPATCH(C)
 #undef C
 #undef R
+#undef B
 }
 
 template <>
