@@ -667,15 +667,19 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
-    // stage the element state, the neighbours' face traces and (curved) the
-    // metrics, in three groups
+    // stage the element state, its own and its neighbours' face traces (the
+    // traces array holds them for every element) and (curved) the metrics, in
+    // three groups
     constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0;
-    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0;
+    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0 &&
+                        (SM::vC * sizeof(Real)) % 16 == 0;
     warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
     cp_async_commit();
+    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-        if (codes[f] >= 0) warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
+        if (!BND || codes[f] >= 0)
+            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
     cp_async_commit();
     if (curved) {
         warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane);
@@ -683,12 +687,9 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane);
     }
     cp_async_commit();
-    cp_async_wait<2>();
-    __syncwarp();
-    // B: own traces (line pass), then neighbour traces and jumps per face point
-    warp_write_traces<DIM, P>(su, sl, op, lane);
     cp_async_wait<1>();
     __syncwarp();
+    // B: jumps per face point
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
@@ -912,9 +913,10 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
                         (SM::rD * sizeof(Real)) % 16 == 0 && (SM::rE * sizeof(Real)) % 16 == 0;
     warp_stage_vol<DIM, P>(su, u + base, lane);
     cp_async_commit();
+    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
-        if (codes[f] >= 0) {
+        if (!BND || codes[f] >= 0) {
             warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
             if constexpr (VISC)
                 warp_stage<NV * NFP, VS>(sm + f * NV * NFP, fvn + int64_t(codes[f] >> 3) * NV * NFP, lane);
@@ -947,10 +949,6 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             }
         }
     }
-    cp_async_wait<1>();
-    __syncwarp();
-    // B0: own traces of every face, one line pass
-    warp_write_traces<DIM, P>(su, sl, op, lane);
     cp_async_wait<0>();
     __syncwarp();
     // B: common normal flux (Rusanov minus common viscous) and jumps
