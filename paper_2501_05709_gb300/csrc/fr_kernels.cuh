@@ -5,12 +5,15 @@
 // kernel are separated by __syncwarp() only.
 //
 // Per RK stage two sweeps (the two BR2 neighbour dependencies force them):
-//   k_visc_face  u, u_f(nbr)  -> own-side viscous normal flux at flux points
-//   k_residual   u, u_f(nbr), viscous fluxes(own, nbr) -> R, fused RK4 stage,
-//                and the flux-point traces u_f of the stage's output state
-// k_traces writes u_f only after the state is set from outside.  Smaller
-// kernels: wall forces, surface sampling, volume integrals, the energy source
-// of Appendix D and the adaptive time step.
+//   k_visc_face  u, u_f(own, nbr)  -> own-side viscous normal flux at flux points
+//   k_residual   u, u_f(own, nbr), viscous fluxes(own, nbr) -> R, fused RK4
+//                stage, and the flux-point traces u_f of the stage's output state
+// k_traces writes u_f only after the state is set from outside.  Both sweeps
+// are compiled per mesh class (metric path, periodic or not; Euler or
+// Navier-Stokes for k_residual), so no dead branch of another class stays in
+// the kernel.  Smaller kernels: wall forces, surface sampling, volume
+// integrals, the energy source of Appendix D, the reduced-degree projection
+// and the adaptive time step.
 // Notation and steps follow Section 2.1 (Eqs. 1-7) with the FR reading
 // described in fr_common.h / fr.h: GL points, DG or g2 correction, Rusanov,
 // BR2, metric terms S = |J| dxi/dx in conservative-curl form.
