@@ -192,6 +192,7 @@ frk::Ops<Real> ops_of(const frg::Ref1D& r) {
         op.hm[j] = Real(r.hm[j]);
         op.hp[j] = Real(r.hp[j]);
         op.w[j] = Real(r.w[j]);
+        op.dlm[j] = Real(frg::lagrange_deriv(r.x, r.np, j, -1.0));
         for (int k = 0; k < r.np; ++k) op.D[j * frk::MAXNP + k] = Real(r.D[j][k]);
         lhm += r.lm[j] * r.hm[j];
         lhp += r.lp[j] * r.hp[j];

@@ -25,6 +25,7 @@ struct Ops {
     Real hm[MAXNP];
     Real hp[MAXNP];
     Real w[MAXNP];
+    Real dlm[MAXNP];  // l_j'(-1), derivative of the basis at the left end
     Real lhm, lhp;
 };
 

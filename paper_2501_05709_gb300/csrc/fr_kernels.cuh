@@ -277,7 +277,8 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 // Regions (Reals) of one warp's shared memory.  F = NF*NV*NFP is one
 // element's face data, U = NV*NSP its state.
 //   visc : A su[U] | B sj[F] | C sl[F] | D sg[max(DIM*U, F)]  (D holds the
-//          staged neighbour traces during the face phase)
+//          staged neighbour traces during the face phase; affine meshes need
+//          no gradient volume, so there D is [F] only)
 //   resid: A su[U] | B sj[max(U,F)] (sd after the gradient) | C sc[F]
 //          (staged own viscous fluxes until each entry is replaced by the
 //          common flux of the same face point) | D sF[max(DIM*U, 2F)] (own +
@@ -292,6 +293,7 @@ struct Smem {
     static constexpr int traces = U;
     static constexpr int vB = U, vC = vB + F, vD = vC + F;
     static constexpr int visc = vD + imax(DIM * U, F);
+    static constexpr int visc_a = vD + F;   // affine: no gradient volume, region D holds the neighbour traces
     static constexpr int rB = U, rC = rB + imax(U, F), rD = rC + F, rE = rD + imax(DIM * U, 2 * F);
     static constexpr int resid = rE + F;
     // curved meshes also stage the element's S [DIM*DIM][NSP] and 1/|J| [NSP]:
@@ -305,7 +307,7 @@ template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_visc(int wpb, bool curved) {
-    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::visc_c : Smem<DIM, P>::visc);
+    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::visc_c : Smem<DIM, P>::visc_a);
 }
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_resid(int wpb, bool curved) {
@@ -657,7 +659,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     using VL = Vol<DIM, P, Real>;
     constexpr bool curved = MP == 0;                // per-point metrics, staged after region D
     constexpr bool diag = MP == 2;                  // affine, diagonal S
-    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc);
+    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc_a);
     Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
     Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
     Real* sg = su + SM::vD;              // gradient          [d or i][v][sp]
@@ -673,7 +675,8 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     // stage the element state, its own and its neighbours' face traces (the
     // traces array holds them for every element) and (curved) the metrics, in
     // three groups
-    constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0;
+    constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0 &&
+                        (SM::visc_a * sizeof(Real)) % 16 == 0;
     constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0 &&
                         (SM::vC * sizeof(Real)) % 16 == 0;
     warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
@@ -721,75 +724,66 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
         }
     }
     __syncwarp();  // the gradient below overwrites the staged neighbour traces
-    // C1: uncorrected reference gradient along lines: q_d = D_d u
+    if constexpr (curved) {
+        // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
+        for (int d = 0; d < DIM; ++d) {
 #pragma unroll 1
-        for (int it = 0; it < NLI; ++it) {
-            const LineTask<DIM, P> tk(lane, it);
-            if (NL % 32 != 0 && tk.t >= NL) break;
-            Real s[NP], q[NP];
-            vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
+            for (int it = 0; it < NLI; ++it) {
+                const LineTask<DIM, P> tk(lane, it);
+                if (NL % 32 != 0 && tk.t >= NL) break;
+                Real s[NP], q[NP];
+                vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
 #pragma unroll
-            for (int i = 0; i < NP; ++i) q[i] = Real(0);
-            apply_D<NP>(op, s, q);
-            vstore_line<DIM, P>(sg + tk.shift, d * NV + tk.vref, d, tk.ln, q);
+                for (int i = 0; i < NP; ++i) q[i] = Real(0);
+                apply_D<NP>(op, s, q);
+                vstore_line<DIM, P>(sg + tk.shift, d * NV + tk.vref, d, tk.ln, q);
+            }
         }
-    }
-    cp_async_wait<0>();
-    __syncwarp();
-    // C2: physical gradient (1/|J|) S^T q at each solution point, in place
+        cp_async_wait<0>();
+        __syncwarp();
+        // C2: physical gradient (1/|J|) S^T q at each solution point, in place
 #pragma unroll 1
-    for (int s = 0; s < NSPW; ++s) {
-        const int sp = lane + 32 * s;
-        if (NSP % 32 != 0 && sp >= NSP) break;
-        Real q[DIM][NV];
+        for (int s = 0; s < NSPW; ++s) {
+            const int sp = lane + 32 * s;
+            if (NSP % 32 != 0 && sp >= NSP) break;
+            Real q[DIM][NV];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d)
+            for (int d = 0; d < DIM; ++d)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) q[d][v] = sg[VL::pt(d * NV + v, sp)];
-        Real S[DIM * DIM];
-        Real iJ;
-        if (curved) {
+                for (int v = 0; v < NV; ++v) q[d][v] = sg[VL::pt(d * NV + v, sp)];
+            Real S[DIM * DIM];
 #pragma unroll
             for (int k = 0; k < DIM * DIM; ++k) S[k] = sS[k * NSP + sp];
-            iJ = sS[DIM * DIM * NSP + sp];
-        } else {
-            load_S<DIM>(g, e, 0, S);
-            iJ = g.iJ[e * g.sJ_e];
-        }
-        if constexpr (diag) {
-            // axis-aligned: the off-diagonal terms are exact zeros
+            const Real iJ = sS[DIM * DIM * NSP + sp];
+            if constexpr (sizeof(Real) == 4) {
+                // pairs of variables as packed FP32x2 (the same order of operations)
+#pragma unroll
+                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                    for (int v = 0; v + 1 < NV; v += 2) {
+                        float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d)
+                            a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]),
+                                           make_float2(q[d][v], q[d][v + 1]), a);
+                        a = __fmul2_rn(a, make_float2(iJ, iJ));
+                        sg[VL::pt(i * NV + v, sp)] = a.x;
+                        sg[VL::pt(i * NV + v + 1, sp)] = a.y;
+                    }
+            }
 #pragma unroll
             for (int i = 0; i < DIM; ++i)
 #pragma unroll
-                for (int v = 0; v < NV; ++v) sg[VL::pt(i * NV + v, sp)] = S[i * DIM + i] * q[i][v] * iJ;
-            continue;
-        }
-        if constexpr (sizeof(Real) == 4) {
-            // pairs of variables as packed FP32x2 (the same order of operations)
+                for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
+                    Real acc = Real(0);
 #pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                for (int v = 0; v + 1 < NV; v += 2) {
-                    float2 a = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d)
-                        a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]), make_float2(q[d][v], q[d][v + 1]), a);
-                    a = __fmul2_rn(a, make_float2(iJ, iJ));
-                    sg[VL::pt(i * NV + v, sp)] = a.x;
-                    sg[VL::pt(i * NV + v + 1, sp)] = a.y;
+                    for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
+                    sg[VL::pt(i * NV + v, sp)] = acc * iJ;
                 }
         }
-#pragma unroll
-        for (int i = 0; i < DIM; ++i)
-#pragma unroll
-            for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
-                Real acc = Real(0);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) acc += S[d * DIM + i] * q[d][v];
-                sg[VL::pt(i * NV + v, sp)] = acc * iJ;
-            }
+    } else {
+        cp_async_wait<0>();
     }
     // normals of this lane's face points, all directions at once
     Real Nr[DIM][NFI][DIM];
@@ -801,6 +795,29 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             const int side = t >= NFP ? 1 : 0;
             if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
         }
+    // affine: per face point of this lane, the derivative coefficients along
+    // the face (rows of D for its two in-face coordinates a, b, and where the
+    // face point's line along a / b starts in the face trace) and across it
+    // (l_j'(-1), or l_j'(+1) = -l_{NP-1-j}'(-1))
+    Real Da[NFI][NP], Db[NFI][NP], dn[NFI][NP];
+    int fa[NFI], fb[NFI];
+    if constexpr (!curved) {
+#pragma unroll
+        for (int it = 0; it < NFI; ++it) {
+            const int t = min(lane + 32 * it, 2 * NFP - 1);
+            const int side = t >= NFP ? 1 : 0;
+            const int fp = t - side * NFP;
+            const int a = fp % NP, b = DIM == 3 ? fp / NP : 0;
+            fa[it] = NP * b;     // line along a: points k + NP b
+            fb[it] = a;          // line along b: points a + NP k
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                Da[it][k] = op.D[a * MAXNP + k];
+                Db[it][k] = op.D[b * MAXNP + k];
+                dn[it][k] = side ? -op.dlm[NP - 1 - k] : op.dlm[k];
+            }
+        }
+    }
     __syncwarp();
     // D: lifted face gradient, viscous normal flux
 #pragma unroll
@@ -837,7 +854,53 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
             }
             Real tr[DIM * NV];   // traces of the physical gradient [i][v]
-            traces_at<DIM, P, DIM * NV>(sg, d, fp, cf, tr);
+            if constexpr (curved) {
+                traces_at<DIM, P, DIM * NV>(sg, d, fp, cf, tr);
+            } else {
+                // affine: the metrics are constant, so the trace of (1/|J|) S^T D u
+                // is (1/|J|) S^T applied to the traces of the reference
+                // derivatives.  Along the face those are the derivatives of the
+                // face trace (interpolation to the face and differentiation along
+                // it commute); across it, the derivative of the normal line at
+                // its end, sum_j l_j'(+-1) u_j.
+                Real q[DIM][NV];
+                const Real* tf = sl + f * NV * NFP;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Real ln[NP];
+                    vload_line<DIM, P>(su, v, d, fp, ln);
+                    Real acc = Real(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) acc += dn[it][j] * ln[j];
+                    q[d][v] = acc;
+                    Real qa = Real(0);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) qa += Da[it][k] * tf[v * NFP + fa[it] + k];
+                    q[d == 0 ? 1 : 0][v] = qa;
+                    if constexpr (DIM == 3) {
+                        Real qb = Real(0);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) qb += Db[it][k] * tf[v * NFP + fb[it] + k * NP];
+                        q[d == 2 ? 1 : 2][v] = qb;
+                    }
+                }
+                Real S[DIM * DIM];
+                load_S<DIM>(g, e, 0, S);
+                const Real iJ = g.iJ[e * g.sJ_e];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        if constexpr (diag) {
+                            tr[i * NV + v] = S[i * DIM + i] * q[i][v] * iJ;
+                        } else {
+                            Real acc = Real(0);
+#pragma unroll
+                            for (int dd = 0; dd < DIM; ++dd) acc += S[dd * DIM + i] * q[dd][v];
+                            tr[i * NV + v] = acc * iJ;
+                        }
+                    }
+            }
             Real G[NV][DIM];
             Real uL[NV];
 #pragma unroll
