@@ -58,6 +58,31 @@ def make_case(name):
         c["nodes"] = np.ascontiguousarray(np.asarray(nodes) @ R.T)
         c.update(p=3, mu=0.02, visc=True)
         c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=10)
+    elif name in ("walls3d_p2", "rotwalls3d_p3"):
+        # straight-sided channel with no-slip walls on both y faces: axis-aligned
+        # (walls3d_p2) or turned about (1, 2, 3) (rotwalls3d_p3)
+        nodes, c["conn"] = W.box_mesh(3, [3, 4, 2], 0.0, [1.5, 1.0, 0.5], q=1, walls_y=True)
+        R = np.eye(3)
+        if name == "rotwalls3d_p3":
+            ax = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
+            K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+            R = np.eye(3) + math.sin(0.5) * K + (1 - math.cos(0.5)) * K @ K
+        c["nodes"] = np.ascontiguousarray(np.asarray(nodes) @ R.T)
+        c.update(p=2 if name == "walls3d_p2" else 3, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=11,
+                                             periods=[1.5, 1.0, 0.5])
+    elif name == "farfield3d_euler_p2":
+        # axis-aligned box with characteristic far field on every face, Euler
+        c["nodes"], c["conn"] = W.box_mesh(3, [3, 3, 2], -1.0, 1.0, q=1, periodic=[False] * 3,
+                                           bc_tag=W.BC_FARFIELD)
+        rho, vel, p = W.freestream(0.3, 5.0)
+        c["freestream"] = (rho, vel, p)
+        c.update(p=2)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=12, periods=[2.0, 2.0, 2.0])
+    elif name == "walls2d_p3":
+        c["nodes"], c["conn"] = W.box_mesh(2, [4, 3], 0.0, [2.0, 1.0], q=1, walls_y=True)
+        c.update(p=3, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=13, periods=[2.0, 1.0])
     elif name == "ns3d_p1":
         c["nodes"], c["conn"] = W.box_mesh(3, 3, 0.0, 1.0, q=1, curve=0.08, seed=8)
         c.update(p=1, mu=0.02, visc=True)
@@ -76,7 +101,8 @@ def make_case(name):
 
 
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
-         "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3"]
+         "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
+         "farfield3d_euler_p2", "walls2d_p3"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):

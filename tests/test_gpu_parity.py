@@ -43,7 +43,8 @@ def test_residual_fp64(name):
     assert relerr(R, R_or) <= fp64_tol(s.residual, u)
 
 
-METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1}
+METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1, "walls3d_p2": 2,
+               "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2}
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -56,7 +57,8 @@ def test_affine_detection(name):
         assert ctx.affine == METRIC_PATH.get(name, 0)
 
 
-@pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2", "rot3d_p3"])
+@pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2", "rot3d_p3",
+                                  "rotwalls3d_p3", "farfield3d_euler_p2"])
 def test_rk4_steps_fp64(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
