@@ -604,7 +604,7 @@ __device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restri
     constexpr int NL = NV * NFP, NLI = (NL + 31) / 32;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-#pragma unroll 1
+#pragma unroll
         for (int it = 0; it < NLI; ++it) {
             const LineTask<DIM, P> tk(lane, it);
             if (NL % 32 != 0 && tk.t >= NL) break;
@@ -728,7 +728,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
         // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-#pragma unroll 1
+#pragma unroll
             for (int it = 0; it < NLI; ++it) {
                 const LineTask<DIM, P> tk(lane, it);
                 if (NL % 32 != 0 && tk.t >= NL) break;
@@ -743,7 +743,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
         cp_async_wait<0>();
         __syncwarp();
         // C2: physical gradient (1/|J|) S^T q at each solution point, in place
-#pragma unroll 1
+#pragma unroll
         for (int s = 0; s < NSPW; ++s) {
             const int sp = lane + 32 * s;
             if (NSP % 32 != 0 && sp >= NSP) break;
@@ -1078,7 +1078,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     if constexpr (VISC) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-#pragma unroll 1
+#pragma unroll
             for (int it = 0; it < NLI; ++it) {
                 const LineTask<DIM, P> tk(lane, it);
                 if (NL % 32 != 0 && tk.t >= NL) break;
@@ -1201,7 +1201,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     // direction by direction
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-#pragma unroll 1
+#pragma unroll
         for (int it = 0; it < NLI; ++it) {
             const LineTask<DIM, P> tk(lane, it);
             if (NL % 32 != 0 && tk.t >= NL) break;
