@@ -195,6 +195,108 @@ def precision_study(steps=25000, dt=4e-5, sample_every=4, n_theta=60, n_r=20, n_
     return out
 
 
+# ---------------------------------------------------------------- Section 3.4: the optimisation loop
+def design_mesh(X, n_theta=60, n_r=20, n_z=2, span=0.2, r_outer=10.0, first_cell=2e-2, pivot=(0.25, 0.0)):
+    """O-grid of the design X = [c_max %, position of c_max (tenths), t_max %,
+    alpha deg] (Section 3.4).  The angle of attack turns the section nose-up
+    about the quarter chord, so that every candidate of a batch shares the
+    free stream along x (lift along y, drag along x).  Returns the nodes,
+    connectivity and the turned trailing edge."""
+    m, pc, t, alpha = float(X[0]) / 100.0, float(X[1]) / 10.0, float(X[2]) / 100.0, float(X[3])
+    nodes, conn = W.ogrid_mesh(n_theta, n_r, n_z, span, r_outer=r_outer, first_cell=first_cell, body="naca",
+                               naca=(m, pc, t))
+    a = math.radians(alpha)
+    ca, sa = math.cos(a), math.sin(a)
+    x0, y0 = pivot
+    X3 = np.array(nodes, float)
+    dx, dy = X3[..., 0] - x0, X3[..., 1] - y0
+    X3[..., 0] = x0 + ca * dx + sa * dy
+    X3[..., 1] = y0 - sa * dx + ca * dy
+    te = (x0 + ca * (1.0 - x0), y0 - sa * (1.0 - x0))
+    return np.ascontiguousarray(X3), conn, te
+
+
+def evaluate_designs(designs, steps=25000, dt=4e-5, sample_every=4, precision=F.FR_FP32, mach=0.2,
+                     reynolds=23000.0, order=3, ncopies=1, seed=0, **mesh_kw):
+    """Mean C_L, mean C_D and the OASPL at the observer 10c below each
+    candidate's trailing edge, for all designs advanced together in one
+    context (the batched poll).  Returns a list of dicts."""
+    import torch
+    meshes, tes = [], []
+    for X in designs:
+        nodes, conn, te = design_mesh(X, **mesh_kw)
+        meshes.append((nodes, conn))
+        tes.append(te)
+    span = mesh_kw.get("span", 0.2)
+    opts, free = naca_options(span, mach, 0.0, reynolds, order, precision, dt)
+    rho, vel, p = free
+    surface = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=span)
+    out = []
+    with F.fr_mesh_load(meshes, opts) as ctx:
+        us = [W.perturbed_uniform(len(n), ctx.nsp, rho, vel, p, amplitude=0.01, seed=seed + k)
+              for k, (n, _) in enumerate(meshes)]
+        F.fr_state_set(ctx, np.concatenate(us))
+        cap = (steps + sample_every - 1) // sample_every
+        hs = [F.fwh_register(ctx, k, surface[0], cap, sample_every) for k in range(len(meshes))]
+        F.fr_rk_step_graph(ctx, steps)
+        torch.cuda.synchronize()
+        forces = [F.fr_forces(ctx, k) for k in range(len(meshes))]
+        hists = [F.fwh_history(ctx, h, len(surface[0])) for h in hs]
+    c0 = math.sqrt(GAMMA * p / rho)
+    mach_vec = np.asarray(vel) / c0
+    for k, X in enumerate(designs):
+        r = {"design": np.asarray(X, float), "cl_mean": forces[k][2], "cd_mean": forces[k][3]}
+        observer = (tes[k][0], tes[k][1] - 10.0, 0.5 * span)
+        try:
+            _, pp, prms, oaspl = oaspl_from_history(hists[k], surface, dt * sample_every, observer, free,
+                                                    mach_vec, span, ncopies)
+            r.update(oaspl_db=oaspl, prms=prms)
+        except F.FrError as e:
+            r.update(oaspl_db=None, prms=None, fwh_error=str(e))
+        out.append(r)
+    return out
+
+
+def optimize_naca(baseline=(0.0, 4.0, 12.0, 6.0), l0=2, max_iter=3, log=None, **eval_kw):
+    """OrthoMADS (Appendix E) on Eq. 8 from the baseline design (NACA 0012 at
+    6 degrees by default), every poll evaluated as one batch on the GPU.  A
+    candidate without an OASPL (empty FW-H window) counts as infeasible."""
+    from . import mads as M
+    base = evaluate_designs([baseline], **eval_kw)[0]
+    if base["oaspl_db"] is None:
+        raise RuntimeError("the baseline run is too short for an FW-H window at the observer")
+    cl0, cd0 = base["cl_mean"], base["cd_mean"]
+    runs = [base]
+
+    def value(r):
+        vals = (r.get("oaspl_db"), r.get("cl_mean"), r.get("cd_mean"))
+        if any(v is None or not math.isfinite(v) for v in vals):
+            return math.inf
+        return M.objective(vals[0], vals[1], vals[2], cl0, cd0)
+
+    def evaluate(points):
+        if len(points) == 1 and np.allclose(M.to_design(points[0]), baseline):
+            return [M.objective(base["oaspl_db"], cl0, cd0, cl0, cd0)]
+        designs = [M.to_design(x) for x in points]
+        try:
+            res = evaluate_designs(designs, **eval_kw)
+        except F.FrError:
+            # a candidate whose mesh or run the library rejects fails alone
+            res = []
+            for X in designs:
+                try:
+                    res.extend(evaluate_designs([X], **eval_kw))
+                except F.FrError as e:
+                    res.append({"design": np.asarray(X, float), "error": str(e)})
+        runs.extend(res)
+        if log:
+            log(res)
+        return [value(r) for r in res]
+
+    out = M.orthomads(evaluate, M.to_scaled(baseline), l0=l0, max_iter=max_iter)
+    return {"baseline": base, "result": out, "design": M.to_design(out.x), "runs": runs}
+
+
 # ---------------------------------------------------------------- Appendix D.1: monopole in a box
 MONOPOLE_SOURCE = [(0.05, 100.0, (0.0, 0.0, 0.0), 0.5)]   # A, k, position, frequency (Eq. D.1)
 
@@ -271,5 +373,14 @@ if __name__ == "__main__":
             r = run_monopole_box(order=order, t_end=12.0)
             res[f"p{order}"] = {k: v for k, v in r.items() if not isinstance(v, np.ndarray)}
         print(json.dumps(res, default=float))
+    elif len(sys.argv) > 1 and sys.argv[1] == "optimize":
+        r = optimize_naca(max_iter=int(sys.argv[2]) if len(sys.argv) > 2 else 3,
+                          log=lambda res: print(json.dumps([{k: v for k, v in x.items()} for x in res],
+                                                           default=lambda a: np.asarray(a).tolist()), flush=True))
+        res = r["result"]
+        print(json.dumps({"baseline": {k: v for k, v in r["baseline"].items()}, "design": r["design"].tolist(),
+                          "f": res.f, "iterations": res.iterations, "evaluations": res.evaluations,
+                          "history": [{k: v for k, v in h.items()} for h in res.history]},
+                         default=lambda a: np.asarray(a).tolist()))
     else:
-        print("usage: python -m paper_2501_05709_gb300.cases naca-precision|monopole-box")
+        print("usage: python -m paper_2501_05709_gb300.cases naca-precision|monopole-box|optimize [iterations]")

@@ -170,7 +170,7 @@ def naca4_surface(m, pc, t, beta):
     x = 0.5 * (1.0 + np.cos(beta))
     yt = 5.0 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2
                     + 0.2843 * x ** 3 - 0.1036 * x ** 4)
-    if m > 0.0:
+    if m != 0.0:
         fore = x < pc
         yc = np.where(fore, m / pc ** 2 * (2 * pc * x - x ** 2),
                       m / (1 - pc) ** 2 * ((1 - 2 * pc) + 2 * pc * x - x ** 2))
