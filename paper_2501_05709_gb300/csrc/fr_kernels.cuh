@@ -1170,30 +1170,31 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             for (int d = 0; d < DIM; ++d)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sF[VL::pt(d * NV + v, sp)] = S[d * DIM + d] * F[v][d];
-            continue;
-        }
-        if constexpr (sizeof(Real) == 4) {
+        } else {
+            if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                    for (int v = 0; v + 1 < NV; v += 2) {
+                        float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+                        for (int i = 0; i < DIM; ++i)
+                            a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]),
+                                           make_float2(F[v][i], F[v + 1][i]), a);
+                        sF[VL::pt(d * NV + v, sp)] = a.x;
+                        sF[VL::pt(d * NV + v + 1, sp)] = a.y;
+                    }
+            }
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
 #pragma unroll
-                for (int v = 0; v + 1 < NV; v += 2) {
-                    float2 a = make_float2(0.0f, 0.0f);
+                for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
+                    Real acc = Real(0);
 #pragma unroll
-                    for (int i = 0; i < DIM; ++i)
-                        a = __ffma2_rn(make_float2(S[d * DIM + i], S[d * DIM + i]), make_float2(F[v][i], F[v + 1][i]), a);
-                    sF[VL::pt(d * NV + v, sp)] = a.x;
-                    sF[VL::pt(d * NV + v + 1, sp)] = a.y;
+                    for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];
+                    sF[VL::pt(d * NV + v, sp)] = acc;
                 }
         }
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-#pragma unroll
-            for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
-                Real acc = Real(0);
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) acc += S[d * DIM + i] * F[v][i];
-                sF[VL::pt(d * NV + v, sp)] = acc;
-            }
     }
     __syncwarp();
     // D+E: per line of direction d, the flux jumps at both ends,
