@@ -1,0 +1,52 @@
+"""Byte accounting behind the roofline figures of bench.py (per element and
+RK stage, p = 3, FP32 unless stated) and the far-field sponge degrees of the
+O-grid workload (host only)."""
+import sys
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def bench():
+    argv = sys.argv
+    sys.argv = argv[:1]
+    try:
+        import bench as B
+    finally:
+        sys.argv = argv
+    return B
+
+
+def test_algorithmic_bytes_per_element(bench):
+    a = bench.algorithmic_bytes(1, 3, 4, viscous=True, curved=False)
+    assert a["visc"] == 5256 and a["resid"] == 11336
+    c = bench.algorithmic_bytes(1, 3, 4, viscous=True, curved=True)
+    assert c["visc"] == 8856 and c["resid"] == 14936
+    d = bench.algorithmic_bytes(1, 3, 8, viscous=True, curved=False)
+    assert d["visc"] == 10488 and d["resid"] == 22648
+    # Euler: no viscous-flux array, no viscous kernel
+    e = bench.algorithmic_bytes(1, 3, 4, viscous=False, curved=False)
+    assert e["visc"] == 0 and e["resid"] == 9416
+    # linear in the element count
+    assert bench.algorithmic_bytes(7, 3, 4)["resid"] == 7 * bench.algorithmic_bytes(1, 3, 4)["resid"]
+
+
+def test_sponge_bytes(bench):
+    # stage arrays read and written (3.5 states on average), traces written, the list entry
+    assert bench.sponge_bytes(1, 3, 4) == 6408
+    assert bench.sponge_bytes(10, 3, 4) == 64080
+
+
+def test_sponge_degrees_of_the_ogrid():
+    from paper_2501_05709_gb300 import workloads as W
+    nodes, _ = W.ogrid_mesh(40, 20, 1, 0.2, r_outer=10.0, first_cell=2e-2)
+    q = W.sponge_orders(nodes, 3)
+    X = np.asarray(nodes)
+    r = np.hypot(X[:, :, 0].mean(axis=1) - 0.5, X[:, :, 1].mean(axis=1))
+    assert q.dtype == np.int32 and q.min() >= 0 and q.max() == 3
+    assert np.all(q[r < 4.0] == 3) and np.all(q[r >= 8.0] == 0)
+    assert np.all(q[(r >= 6.0) & (r < 8.0)] == 1)
+    # never rises with the distance from the body
+    order = np.argsort(r)
+    assert np.all(np.diff(q[order]) <= 0)
