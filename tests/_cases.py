@@ -48,7 +48,7 @@ def make_case(name):
         nsp = (c["p"] + 1) ** 3
         E = len(c["nodes"])
         c["state"] = lambda x: W.perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.02, seed=0)
-    elif name == "rot3d_p3":
+    elif name in ("rot3d_p3", "rot3d_euler_p2"):
         # a periodic box turned about (1, 2, 3): affine but not axis-aligned
         # (full metric matrices); the state is periodic in the box's own frame
         ax = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
@@ -56,7 +56,10 @@ def make_case(name):
         R = np.eye(3) + math.sin(0.5) * K + (1 - math.cos(0.5)) * K @ K
         nodes, c["conn"] = W.box_mesh(3, [4, 3, 3], 0.0, 1.0, q=1)
         c["nodes"] = np.ascontiguousarray(np.asarray(nodes) @ R.T)
-        c.update(p=3, mu=0.02, visc=True)
+        if name == "rot3d_p3":
+            c.update(p=3, mu=0.02, visc=True)
+        else:
+            c.update(p=2)
         c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=10)
     elif name in ("walls3d_p2", "rotwalls3d_p3"):
         # straight-sided channel with no-slip walls on both y faces: axis-aligned
@@ -102,7 +105,7 @@ def make_case(name):
 
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
-         "farfield3d_euler_p2", "walls2d_p3"]
+         "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):

@@ -44,7 +44,7 @@ def test_residual_fp64(name):
 
 
 METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1, "walls3d_p2": 2,
-               "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2}
+               "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2, "rot3d_euler_p2": 1}
 
 
 @pytest.mark.parametrize("name", CASES)
