@@ -81,7 +81,10 @@ class FRSolver:
     # -------------------------------------------------------------------
     def residual(self, u, want_faces=False, t=0.0):
         """R(u) for u [E, nvar, Nsp] at time t (the time enters only through
-        the source term); optionally also face data for forces."""
+        the source term); optionally also face data: the traces ``uf``
+        [E, nface, nvar, Nfp], the common viscous normal flux ``Fv_common``
+        and the BR2 face gradients ``Gface`` [E, nface, nvar, dim, Nfp]
+        (None for inviscid physics), and the boundary states ``bc``."""
         m, ph = self.m, self.ph
         ref = m.ref
         E, dim, Np, Nfp, nf = m.E, m.dim, m.Np, m.Nfp, m.nface
@@ -128,6 +131,7 @@ class FRSolver:
         # 4. viscous terms (BR2)
         grad = None
         Fv_common = None
+        Gface = None
         if ph.viscous:
             qD = [_deriv(ut, ref.D, d, dim).reshape(E, nv, -1) for d in range(dim)]
             gD = np.zeros((E, nv, dim, m.Nsp))
@@ -197,7 +201,7 @@ class FRSolver:
             R = project(m, R, self.caps)
         if not want_faces:
             return R
-        return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc}
+        return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc, "Gface": Gface}
 
     # -------------------------------------------------------------------
     def rk4_step(self, u, dt, t=0.0):

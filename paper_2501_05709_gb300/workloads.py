@@ -18,8 +18,10 @@ Mesh description (the layout ``fr_mesh_load`` takes):
   ``2*d+1`` is xi_d = +1.  An interior face holds ``(neighbour element,
   neighbour face, orientation)``; a boundary face holds ``(-tag, 0, 0)`` with
   tag ``BC_WALL`` (no-slip adiabatic wall) or ``BC_FARFIELD``
-  (characteristic far field).  Every generator here emits orientation 0
-  (face points correspond one to one in the same order).
+  (characteristic far field).  The structured generators emit orientation 0
+  (face points correspond one to one in the same order); ``reorient`` turns
+  every element's local frame by a seeded rotation of the reference square or
+  cube, which gives the faces every orientation code.
 
 Workload recipes (paper Section 3.1 and Appendix C shapes):
 
@@ -157,6 +159,156 @@ def box_mesh(dim, n, lo, hi, q=1, periodic=None, walls_y=False, curve=0.0, seed=
     bc = [BC_WALL if bc_tag is None else bc_tag] * dim
     conn = _structured_conn(ne, periodic, bc, bc)
     return nodes, conn
+
+
+def proper_rotations(dim):
+    """The proper rotations of the reference square (4) or cube (24), each as
+    (perm, sign): old coordinate xi[perm[k]] = sign[k] * new coordinate xi'[k].
+    Reflections are left out: they would make the element map left-handed
+    (negative Jacobian)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(dim)):
+        # parity of the permutation
+        inv = sum(1 for i in range(dim) for j in range(i + 1, dim) if perm[i] > perm[j])
+        for sign in itertools.product((1, -1), repeat=dim):
+            if (-1) ** inv * int(np.prod(sign)) == 1:
+                out.append((tuple(perm), tuple(sign)))
+    return out
+
+
+def _old_index(new_idx, rot, n):
+    """Old tensor multi-index of new multi-index new_idx (tuple over directions)
+    of an n-point-per-direction tensor grid under rotation rot (symmetric
+    points: reversal maps index i to n-1-i)."""
+    perm, sign = rot
+    old = [0] * len(perm)
+    for k, (pk, sk) in enumerate(zip(perm, sign)):
+        old[pk] = new_idx[k] if sk > 0 else n - 1 - new_idx[k]
+    return tuple(old)
+
+
+def _lin(idx, n):
+    """Linear index i_0 + n i_1 (+ n^2 i_2): direction 0 fastest."""
+    return sum(int(i) * n ** d for d, i in enumerate(idx))
+
+
+def tensor_relabel(n, dim, rot):
+    """Index array r with new_values[..., k] = old_values[..., r[k]] for the
+    points of an n^dim tensor grid on the symmetric reference element."""
+    out = np.empty(n ** dim, np.int64)
+    for k in range(n ** dim):
+        idx = tuple((k // n ** d) % n for d in range(dim))
+        out[k] = _lin(_old_index(idx, rot, n), n)
+    return out
+
+
+def _face_point_index(dim, d, idx, n):
+    """Face point index of tensor multi-index idx on a face normal to d: the
+    remaining directions in increasing order, the lower one fastest."""
+    rest = [idx[k] for k in range(dim) if k != d]
+    return _lin(rest, n)
+
+
+def _orientation_map(dim, n, o, fp):
+    """Neighbour face point of face point fp for orientation code o (the
+    mesh-description convention: dim 2 bit 0 reverses; dim 3 bit 2 swaps the
+    two face indices, then bit 0 / bit 1 reverse the first / second)."""
+    if dim == 2:
+        return n - 1 - fp if o & 1 else fp
+    a, b = fp % n, fp // n
+    if o & 4:
+        a, b = b, a
+    if o & 1:
+        a = n - 1 - a
+    if o & 2:
+        b = n - 1 - b
+    return a + n * b
+
+
+def reorient(nodes, conn, dim, seed=0, rots=None, nfp_check=3):
+    """Turn every element's local frame by a proper rotation of the reference
+    element (seeded choice, or rots[e] = (perm, sign)) and rebuild the face
+    connectivity with the orientation codes that result.
+
+    Returns (nodes', conn', rots).  The physical mesh is unchanged; only the
+    labelling of each element's nodes, faces and face points changes, so any
+    discretisation that is invariant under the symmetries of the reference
+    element gives the same solution, relabelled point by point with
+    ``tensor_relabel(p+1, dim, rots[e])``.  The base mesh must carry
+    orientation 0.  ``nfp_check`` points per face direction are used to derive
+    each code (any n >= 3 fixes it uniquely)."""
+    nodes = np.asarray(nodes, float)
+    conn = np.asarray(conn, np.int32)
+    E, nn, _ = nodes.shape
+    q = int(round(nn ** (1.0 / dim))) - 1
+    if np.any(conn[:, :, 0] >= 0) and np.any(conn[conn[:, :, 0] >= 0][:, 2] != 0):
+        raise ValueError("reorient needs a base mesh with orientation 0")
+    allr = proper_rotations(dim)
+    if rots is None:
+        rng = np.random.default_rng(seed)
+        rots = [allr[k] for k in rng.integers(0, len(allr), E)]
+    rots = [(tuple(r[0]), tuple(r[1])) for r in rots]
+    new_nodes = np.empty_like(nodes)
+    for e in range(E):
+        new_nodes[e] = nodes[e][tensor_relabel(q + 1, dim, rots[e])]
+    n = nfp_check
+
+    def new_face_of_old(e, f_old):
+        perm, sign = rots[e]
+        d_old, s_old = divmod(f_old, 2)
+        k = perm.index(d_old)                       # new direction along old d
+        s_new = s_old if sign[k] > 0 else 1 - s_old
+        return 2 * k + s_new
+
+    def old_fp_table(e, f_new):
+        """old face point index (old face of e) of each new face point."""
+        dn, sn = divmod(f_new, 2)
+        out = []
+        others = [k for k in range(dim) if k != dn]
+        for fp in range(n ** (dim - 1)):
+            idx = [0] * dim
+            for j, k in enumerate(others):
+                idx[k] = (fp // n ** j) % n
+            idx[dn] = n - 1 if sn else 0
+            old = _old_index(tuple(idx), rots[e], n)
+            d_old = rots[e][0][dn]
+            out.append(_face_point_index(dim, d_old, old, n))
+        return out
+
+    new_conn = np.zeros_like(conn)
+    ncode = 2 if dim == 2 else 8
+    for e in range(E):
+        perm, sign = rots[e]
+        for f_new in range(2 * dim):
+            dn, sn = divmod(f_new, 2)
+            d_old = perm[dn]
+            s_old = sn if sign[dn] > 0 else 1 - sn
+            f_old = 2 * d_old + s_old
+            ne, nf_old, _ = conn[e, f_old]
+            if ne < 0:
+                new_conn[e, f_new] = conn[e, f_old]
+                continue
+            nf_new = new_face_of_old(ne, nf_old)
+            mine = old_fp_table(e, f_new)            # my new fp -> old fp (shared, orientation 0)
+            theirs = old_fp_table(ne, nf_new)        # their new fp -> old fp
+            inv = {o: k for k, o in enumerate(theirs)}
+            want = [inv[o] for o in mine]
+            code = [o for o in range(ncode)
+                    if all(_orientation_map(dim, n, o, k) == want[k] for k in range(len(want)))]
+            if len(code) != 1:
+                raise RuntimeError("no unique orientation code for a face")
+            new_conn[e, f_new] = (ne, nf_new, code[0])
+    return np.ascontiguousarray(new_nodes), new_conn, rots
+
+
+def relabel_points(a, rots, n, dim):
+    """Values a [E, ..., n^dim] at an element's tensor points in the base
+    labelling -> the labelling of ``reorient``'s rotated elements."""
+    out = np.empty_like(a)
+    for e, r in enumerate(rots):
+        out[e] = a[e][..., tensor_relabel(n, dim, r)]
+    return out
 
 
 def naca4_surface(m, pc, t, beta):

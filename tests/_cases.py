@@ -94,6 +94,32 @@ def make_case(name):
         c["nodes"], c["conn"] = W.box_mesh(3, [3, 2, 2], 0.0, 1.0, q=2, curve=0.1, seed=9)
         c.update(p=4, kind=1, mu=0.02, visc=True)
         c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=8)
+    elif name in ("turned3d_curved_p3", "turned3d_affine_p3", "turned2d_curved_p2_g2"):
+        # every element's local frame turned by a seeded rotation of the
+        # reference element: faces carry all orientation codes
+        if name == "turned3d_curved_p3":
+            nodes, conn = W.box_mesh(3, 3, 0.0, 1.0, q=2, curve=0.1, seed=3)
+            c.update(p=3, mu=0.02, visc=True)
+        elif name == "turned3d_affine_p3":
+            nodes, conn = W.box_mesh(3, [4, 3, 3], 0.0, 1.0, q=1)
+            c.update(p=3, mu=0.02, visc=True)
+        else:
+            nodes, conn = W.box_mesh(2, [4, 3], 0.0, 1.0, q=2, curve=0.1, seed=2)
+            c.update(p=2, kind=1, mu=0.01, visc=True)
+        c["nodes"], c["conn"], _ = W.reorient(nodes, conn, len(nodes[0][0]), seed=5)
+        c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=14)
+    elif name in ("turned_ogrid_p3", "turned_ogrid_euler_p2"):
+        nodes, conn = W.ogrid_mesh(12, 3, 2, 0.2, r_outer=3.0, first_cell=0.05)
+        c["nodes"], c["conn"], _ = W.reorient(nodes, conn, 3, seed=8)
+        rho, vel, p = W.freestream(0.2, 3.0)
+        c["freestream"] = (rho, vel, p)
+        if name == "turned_ogrid_p3":
+            c.update(p=3, mu=1.0 / 2300.0, visc=True, dt=2e-4)
+        else:
+            c.update(p=2, dt=2e-4)
+        nsp = (c["p"] + 1) ** 3
+        E = len(c["nodes"])
+        c["state"] = lambda x: W.perturbed_uniform(E, nsp, rho, vel, p, amplitude=0.02, seed=1)
     elif name == "single_element":
         c["nodes"], c["conn"] = W.box_mesh(3, 1, 0.0, 1.0, q=1)
         c.update(p=3, mu=0.02, visc=True)
@@ -105,7 +131,8 @@ def make_case(name):
 
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
-         "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2"]
+         "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2", "turned3d_curved_p3", "turned3d_affine_p3",
+         "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):

@@ -44,7 +44,8 @@ def test_residual_fp64(name):
 
 
 METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1, "walls3d_p2": 2,
-               "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2, "rot3d_euler_p2": 1}
+               "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2, "rot3d_euler_p2": 1,
+               "turned3d_affine_p3": 1}
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -58,7 +59,8 @@ def test_affine_detection(name):
 
 
 @pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2", "rot3d_p3",
-                                  "rotwalls3d_p3", "farfield3d_euler_p2"])
+                                  "rotwalls3d_p3", "farfield3d_euler_p2", "turned3d_curved_p3", "turned_ogrid_p3",
+                                  "turned2d_curved_p2_g2"])
 def test_rk4_steps_fp64(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
@@ -113,9 +115,10 @@ def test_conservation_on_gpu(name):
     assert np.all(np.abs(after[:nv] - before[:nv]) <= 1e-12 * scale)
 
 
-def test_forces_match_oracle():
+@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3"])
+def test_forces_match_oracle(name):
     from paper_2501_05709_gb300 import fr as F
-    c = make_case("ns3d_ogrid_p3")
+    c = make_case(name)
     m, s = oracle_for(c)
     u = c["state"](m.xsp)
     Fo = s.wall_force(u)
@@ -137,11 +140,12 @@ def test_forces_match_oracle():
     assert out[4] == 1.0
 
 
-def test_sampling_matches_oracle():
+@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3"])
+def test_sampling_matches_oracle(name):
     from oracle.sampling import locate, sample
     from paper_2501_05709_gb300 import fr as F
     from paper_2501_05709_gb300 import workloads as W
-    c = make_case("ns3d_ogrid_p3")
+    c = make_case(name)
     m, s = oracle_for(c)
     u = c["state"](m.xsp)
     y, _, _ = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.05, span=0.2)

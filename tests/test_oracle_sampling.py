@@ -12,9 +12,10 @@ def test_sampling_exact_for_linear_field_on_curved_ogrid():
     m = Mesh(nodes, conn, 3)
     x = m.xsp
     rho = 1.0 + 0.1 * x[..., 0] - 0.05 * x[..., 1]
-    V = np.stack([0.5 + 0.02 * x[..., 1], -0.1 + 0.03 * x[..., 0], 0.01 * x[..., 2] + 0 * rho])
-    # conserved variables linear in x: rho, rho V (quadratic but p=3 >= 2*2? no:)
-    # sample conserved-linear fields instead: choose rho V linear, rho E linear
+    # conserved variables linear in x (rho, rho V, rho E): of degree 2 in xi
+    # on these quadratic elements, so this checks the point location and the
+    # interpolation up to degree 2 (test_oracle_boundaries checks exactness on
+    # tensor polynomials of the full degree p)
     u = np.zeros((m.E, 5, m.Nsp))
     u[:, 0] = rho
     u[:, 1] = 0.5 + 0.02 * x[..., 1]
@@ -31,7 +32,6 @@ def test_sampling_exact_for_linear_field_on_curved_ogrid():
     assert np.allclose(s[:, 0], r, atol=1e-12, rtol=0)
     assert np.allclose(s[:, 1:4], mom / r[:, None], atol=1e-12, rtol=0)
     assert np.allclose(s[:, 4], p, atol=1e-12, rtol=0)
-    del V
 
 
 def test_locate_recovers_solution_point_positions():
