@@ -51,10 +51,14 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(n=4, min_seconds=10.0, max_steps=10000, warmup=1):
+ORACLE_BOX = 8   # elements per direction of the oracle's sample of the TGV box
+
+
+def oracle_sample(n=ORACLE_BOX, min_seconds=10.0, max_steps=10000, warmup=1):
     """FP64 numpy oracle: RK4 steps of the same TGV workload on an n^3 box,
     one BLAS thread, for at least min_seconds (and at most max_steps steps);
-    returns (DOF*stages/s, steps, seconds, dof)."""
+    min_seconds <= 0 runs exactly max_steps steps.  Returns (DOF*stages/s,
+    steps, seconds, dof)."""
     import numpy as np
 
     from oracle.fr import FRSolver
@@ -69,7 +73,7 @@ def oracle_sample(n=4, min_seconds=10.0, max_steps=10000, warmup=1):
         u = s.rk4_step(u, DT)
     t0 = time.perf_counter()
     k = 0
-    while k < max_steps and (time.perf_counter() - t0 < min_seconds or k == 0):
+    while k < max_steps and (min_seconds <= 0 or time.perf_counter() - t0 < min_seconds or k == 0):
         u = s.rk4_step(u, DT)
         k += 1
     dt = time.perf_counter() - t0
@@ -87,7 +91,9 @@ def run_oracle_subprocess(min_seconds, max_steps=10000, warmup=1):
         raise RuntimeError(r.stderr[-2000:])
     v, k, dt, dof = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"TGV p=3 on a 4^3-element box ({dof} DOF), {k} RK4 steps in {dt:.1f} s, numpy FP64, 1 BLAS thread"}
+            "steps_timed": k, "seconds": dt,
+            "sample": f"TGV p=3 on a {ORACLE_BOX}^3-element box ({dof} DOF; the same per-element work as the "
+                      f"32^3 workload), {k} RK4 steps in {dt:.1f} s, numpy FP64, 1 BLAS thread"}
 
 
 def run_oracle_all_cores(min_seconds):
@@ -113,7 +119,7 @@ def run_oracle_all_cores(min_seconds):
         steps += k
         secs = max(secs, dt)
     return {"value": float(sum(rates)), "unit": UNIT, "cores": ncores, "kind": "oracle",
-            "sample": f"{ncores} concurrent single-threaded processes, each TGV p=3 on a 4^3-element box "
+            "sample": f"{ncores} concurrent single-threaded processes, each TGV p=3 on a {ORACLE_BOX}^3-element box "
                       f"({dof} DOF) for >= {min_seconds:.0f} s ({steps} RK4 steps in total), numpy FP64"}
 
 
@@ -581,10 +587,12 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # each step: one RK4 step of the 4^3-element sample of the same workload
+        # each step: one RK4 step of the 8^3-element sample of the same workload
+        # (exactly --steps timed steps after --warmup untimed ones)
         cb = run_oracle_subprocess(min_seconds=0.0, max_steps=args.steps, warmup=args.warmup)
         line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": 1e3 * cb["seconds"] / max(cb["steps_timed"], 1),
+                "impl": "reference", "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}}

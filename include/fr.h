@@ -280,9 +280,11 @@ int fwh_integrate(const double* hist, int nt, int npts, const double* y, const d
  *   - Limit: 8*npts*nt + ceil(npts / max(1, 32/ncopies)) * (longest
  *     observer window) must not exceed 2^22; larger problems get FR_EINVAL
  *     with a message naming the sizes (use fwh_integrate for them).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current
+ *     device's context (cudaGetSymbolAddress, which allocates nothing), so
+ *     the address is never stale, e.g. after cudaDeviceReset.  Like
+ *     fwh_integrate, the call reads the panel positions back to the host
+ *     and synchronises the stream before it returns.
  *   - Every call on a device shares the one array: calls that overlap on
  *     the GPU (other streams or threads) race and give wrong results.  Each
  *     call writes all the scratch it reads, so nothing needs clearing.

@@ -17,7 +17,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -245,10 +244,23 @@ __global__ void k_fwh_reduce(const double* __restrict__ partial, int ngroups, in
 // records the message returned by fr_last_error (defined with the context code)
 int fr_set_error_from_fwh(int code, const char* msg);
 
-extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double* y, const double* n,
-                             const double* dS, double dtau, double tau0, const double* obs, int nobs,
-                             const double Minf[3], double c0, double rho0, double p0, double Lspan,
-                             int ncopies, double* p_out, int cap, int* nt_out, double* t0_out, void* stream) {
+namespace {
+
+// Host-side plan of one FW-H integration: the constants of Eqs. B.8-B.12,
+// every observer's unified window (Eq. B.13 and the text after it: from the
+// latest first arrival to the earliest last arrival over all panel copies),
+// and the panel grouping of the accumulation kernel.
+struct FwhPlan {
+    FwhConst k;
+    std::vector<double> tstart;   // first unified time per observer
+    std::vector<int> Tn;          // unified samples per observer
+    int group = 1, ngroups = 1, Tmax = 0;
+};
+
+int fwh_plan(int nt, int npts, const double* y, const double* n, const double* dS, const double* hist, double dtau,
+             double tau0, const double* obs, int nobs, const double Minf[3], double c0, double rho0, double p0,
+             double Lspan, int ncopies, const double* p_out, int cap, const int* nt_out, const double* t0_out,
+             cudaStream_t s, FwhPlan& pl) {
     if (!hist || !y || !n || !dS || !obs || !Minf || !p_out || !nt_out || !t0_out)
         return fr_set_error_from_fwh(FR_EINVAL, "null argument");
     if (nt < 5 || npts < 1 || nobs < 1 || cap < 1 || ncopies < 1 || ncopies % 2 == 0 || !(dtau > 0.0) ||
@@ -256,8 +268,7 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
         return fr_set_error_from_fwh(FR_EINVAL, "bad sizes (nt >= 5, odd ncopies, dtau > 0, c0 > 0 required)");
     const double MM = Minf[0] * Minf[0] + Minf[1] * Minf[1] + Minf[2] * Minf[2];
     if (!(MM < 1.0)) return fr_set_error_from_fwh(FR_EINVAL, "|Minf| must be below 1");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    FwhConst k;
+    FwhConst& k = pl.k;
     for (int i = 0; i < 3; ++i) k.M[i] = Minf[i];
     k.c0 = c0;
     k.rho0 = rho0;
@@ -271,8 +282,8 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
         cudaStreamSynchronize(s) != cudaSuccess)
         return fr_set_error_from_fwh(FR_ECUDA, "cannot read panel positions");
     const int K = (ncopies - 1) / 2;
-    std::vector<double> tstart(nobs);
-    std::vector<int> Tn(nobs);
+    pl.tstart.assign(nobs, 0.0);
+    pl.Tn.assign(nobs, 0);
     for (int o = 0; o < nobs; ++o) {
         double dmax = -1e300, dmin = 1e300;
         for (int p = 0; p < npts; ++p)
@@ -294,74 +305,93 @@ extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double*
         if (te < ts) return fr_set_error_from_fwh(FR_EWINDOW, "empty observer window");
         const int T = int(std::floor((te - ts) / dtau + 1e-9)) + 1;
         if (T > cap) return fr_set_error_from_fwh(FR_EWINDOW, "observer window longer than the output capacity");
-        tstart[o] = ts;
-        Tn[o] = T;
+        pl.tstart[o] = ts;
+        pl.Tn[o] = T;
     }
-    const int group = std::max(1, kFwhGroup / ncopies);
-    const int ngroups = (npts + group - 1) / group;
+    pl.group = std::max(1, kFwhGroup / ncopies);
+    pl.ngroups = (npts + pl.group - 1) / pl.group;
     if ((cap + 128 * FWH_KO - 1) / (128 * FWH_KO) > 65535)
         return fr_set_error_from_fwh(FR_EINVAL, "observer window too long for one launch");
-    int Tmax = *std::max_element(Tn.begin(), Tn.end());
-    double *X = nullptr, *partial = nullptr;
-    if (cudaMalloc(&X, sizeof(double) * size_t(npts) * NSER * nt) != cudaSuccess ||
-        cudaMalloc(&partial, sizeof(double) * size_t(ngroups) * Tmax) != cudaSuccess) {
-        if (X) cudaFree(X);
-        return fr_set_error_from_fwh(FR_ENOMEM, "cannot allocate FW-H scratch");
-    }
+    pl.Tmax = *std::max_element(pl.Tn.begin(), pl.Tn.end());
+    return FR_OK;
+}
+
+// Scratch of a plan: the source series X [npts][NSER][nt] and one partial-sum
+// row per panel group [ngroups][Tmax], in doubles.
+size_t fwh_series_doubles(int npts, int nt) { return size_t(npts) * NSER * nt; }
+size_t fwh_partial_doubles(const FwhPlan& pl) { return size_t(pl.ngroups) * pl.Tmax; }
+
+// The kernels of one integration on scratch X / partial (both fully written
+// before they are read), then a synchronisation of the stream.
+int fwh_run(const FwhPlan& pl, const double* hist, int nt, int npts, const double* y, const double* n,
+            const double* dS, const double* obs, int nobs, double Lspan, int ncopies, double* p_out, int cap,
+            int* nt_out, double* t0_out, double* X, double* partial, cudaStream_t s) {
     const int64_t nw = int64_t(nt) * npts;
-    k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
-    const size_t sm = FWH_SH_BYTES * size_t(group) * ncopies;
+    k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, pl.k, X);
+    const size_t sm = FWH_SH_BYTES * size_t(pl.group) * ncopies;
     cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess && sm > 48 * 1024)
         err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
-        dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
-        k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
-                                          tstart[o], Tn[o], ncopies, Lspan, group, partial);
-        k_fwh_reduce<<<unsigned((Tn[o] + 31) / 32), dim3(32, 32), 0, s>>>(partial, ngroups, Tn[o],
-                                                                          p_out + size_t(o) * cap);
+        dim3 grid(unsigned(pl.ngroups), unsigned((pl.Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
+        k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, pl.k, obs[o * 3 + 0], obs[o * 3 + 1],
+                                          obs[o * 3 + 2], pl.tstart[o], pl.Tn[o], ncopies, Lspan, pl.group,
+                                          partial);
+        k_fwh_reduce<<<unsigned((pl.Tn[o] + 31) / 32), dim3(32, 32), 0, s>>>(partial, pl.ngroups, pl.Tn[o],
+                                                                             p_out + size_t(o) * cap);
         err = cudaGetLastError();
-        nt_out[o] = Tn[o];
-        t0_out[o] = tstart[o];
+        nt_out[o] = pl.Tn[o];
+        t0_out[o] = pl.tstart[o];
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-    cudaFree(X);
-    cudaFree(partial);
     if (err != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, cudaGetErrorString(err));
     return FR_OK;
+}
+
+}  // namespace
+
+extern "C" int fwh_integrate(const double* hist, int nt, int npts, const double* y, const double* n,
+                             const double* dS, double dtau, double tau0, const double* obs, int nobs,
+                             const double Minf[3], double c0, double rho0, double p0, double Lspan,
+                             int ncopies, double* p_out, int cap, int* nt_out, double* t0_out, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FwhPlan pl;
+    int rc = fwh_plan(nt, npts, y, n, dS, hist, dtau, tau0, obs, nobs, Minf, c0, rho0, p0, Lspan, ncopies, p_out,
+                      cap, nt_out, t0_out, s, pl);
+    if (rc != FR_OK) return rc;
+    double *X = nullptr, *partial = nullptr;
+    if (cudaMalloc(&X, sizeof(double) * fwh_series_doubles(npts, nt)) != cudaSuccess ||
+        cudaMalloc(&partial, sizeof(double) * fwh_partial_doubles(pl)) != cudaSuccess) {
+        if (X) cudaFree(X);
+        return fr_set_error_from_fwh(FR_ENOMEM, "cannot allocate FW-H scratch");
+    }
+    rc = fwh_run(pl, hist, nt, npts, y, n, dS, obs, nobs, Lspan, ncopies, p_out, cap, nt_out, t0_out, X, partial, s);
+    cudaFree(X);
+    cudaFree(partial);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
 // fwh_integrate_noalloc: the same computation with its scratch (the source
 // series and the partial sums) in a fixed file-scope device array, for callers
-// that cannot call cudaMalloc/cudaFree.  Host code must not pass the array's
-// name to a kernel (on the host it is only a stand-in); its device address is
-// looked up once per device with cudaGetSymbolAddress and cached.
+// that cannot call cudaMalloc/cudaFree.  On the host the array's name is only
+// a stand-in, never a device address: every call looks the address up on the
+// current device with cudaGetSymbolAddress (which allocates nothing), so the
+// address always belongs to the context the kernels run in.
 
 namespace {
 
 constexpr size_t kNoallocScratchDoubles = size_t(1) << 22;  // 32 MiB per device
 __device__ __align__(256) double g_fwh_scratch[kNoallocScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_fwh_scratch on the current device (set-up on first use).
+// Device address of g_fwh_scratch in the current device's context.
 int noalloc_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, "no current CUDA device");
-    if (dev < 0 || dev >= kMaxDevices) return fr_set_error_from_fwh(FR_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_fwh_scratch);
-        if (e != cudaSuccess || !p)
-            return fr_set_error_from_fwh(FR_ECUDA, (std::string("cudaGetSymbolAddress of the FW-H scratch: ") +
-                                                    cudaGetErrorString(e)).c_str());
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fwh_scratch);
+    if (e != cudaSuccess || !p)
+        return fr_set_error_from_fwh(FR_ECUDA, (std::string("cudaGetSymbolAddress of the FW-H scratch: ") +
+                                                cudaGetErrorString(e)).c_str());
+    *out = static_cast<double*>(p);
     return FR_OK;
 }
 
@@ -372,87 +402,21 @@ extern "C" int fwh_integrate_noalloc(const double* hist, int nt, int npts, const
                                      const double Minf[3], double c0, double rho0, double p0, double Lspan,
                                      int ncopies, double* p_out, int cap, int* nt_out, double* t0_out,
                                      void* stream) {
-    if (!hist || !y || !n || !dS || !obs || !Minf || !p_out || !nt_out || !t0_out)
-        return fr_set_error_from_fwh(FR_EINVAL, "null argument");
-    if (nt < 5 || npts < 1 || nobs < 1 || cap < 1 || ncopies < 1 || ncopies % 2 == 0 || !(dtau > 0.0) ||
-        !(c0 > 0.0))
-        return fr_set_error_from_fwh(FR_EINVAL, "bad sizes (nt >= 5, odd ncopies, dtau > 0, c0 > 0 required)");
-    const double MM = Minf[0] * Minf[0] + Minf[1] * Minf[1] + Minf[2] * Minf[2];
-    if (!(MM < 1.0)) return fr_set_error_from_fwh(FR_EINVAL, "|Minf| must be below 1");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    FwhConst k;
-    for (int i = 0; i < 3; ++i) k.M[i] = Minf[i];
-    k.c0 = c0;
-    k.rho0 = rho0;
-    k.p0 = p0;
-    k.dtau = dtau;
-    k.tau0 = tau0;
-    k.b2 = 1.0 / (1.0 - MM);
-    std::vector<double> yh(size_t(npts) * 3);
-    if (cudaMemcpyAsync(yh.data(), y, yh.size() * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return fr_set_error_from_fwh(FR_ECUDA, "cannot read panel positions");
-    const int K = (ncopies - 1) / 2;
-    std::vector<double> tstart(nobs);
-    std::vector<int> Tn(nobs);
-    for (int o = 0; o < nobs; ++o) {
-        double dmax = -1e300, dmin = 1e300;
-        for (int p = 0; p < npts; ++p)
-            for (int cc = -K; cc <= K; ++cc) {
-                double r[3] = {obs[o * 3 + 0] - yh[p * 3 + 0], obs[o * 3 + 1] - yh[p * 3 + 1],
-                               obs[o * 3 + 2] - (yh[p * 3 + 2] + cc * Lspan)};
-                double Mr = 0, rr = 0;
-                for (int i = 0; i < 3; ++i) {
-                    Mr += Minf[i] * r[i];
-                    rr += r[i] * r[i];
-                }
-                const double Rs = std::sqrt(rr + k.b2 * Mr * Mr) / std::sqrt(k.b2);
-                const double d = k.b2 * (Rs - Mr) / c0;
-                dmax = std::max(dmax, d);
-                dmin = std::min(dmin, d);
-            }
-        const double ts = tau0 + dmax;
-        const double te = tau0 + (nt - 1) * dtau + dmin;
-        if (te < ts) return fr_set_error_from_fwh(FR_EWINDOW, "empty observer window");
-        const int T = int(std::floor((te - ts) / dtau + 1e-9)) + 1;
-        if (T > cap) return fr_set_error_from_fwh(FR_EWINDOW, "observer window longer than the output capacity");
-        tstart[o] = ts;
-        Tn[o] = T;
-    }
-    const int group = std::max(1, kFwhGroup / ncopies);
-    const int ngroups = (npts + group - 1) / group;
-    if ((cap + 128 * FWH_KO - 1) / (128 * FWH_KO) > 65535)
-        return fr_set_error_from_fwh(FR_EINVAL, "observer window too long for one launch");
-    const int Tmax = *std::max_element(Tn.begin(), Tn.end());
-    // the series (8 per panel and source time) and one partial row per panel
-    // group must fit the fixed scratch; both are fully written before any read
-    const size_t need = size_t(npts) * NSER * nt + size_t(ngroups) * Tmax;
+    FwhPlan pl;
+    int rc = fwh_plan(nt, npts, y, n, dS, hist, dtau, tau0, obs, nobs, Minf, c0, rho0, p0, Lspan, ncopies, p_out,
+                      cap, nt_out, t0_out, s, pl);
+    if (rc != FR_OK) return rc;
+    // the series and the partial rows must fit the fixed scratch
+    const size_t need = fwh_series_doubles(npts, nt) + fwh_partial_doubles(pl);
     if (need > kNoallocScratchDoubles)
         return fr_set_error_from_fwh(
             FR_EINVAL, ("fwh_integrate_noalloc: needs " + std::to_string(need) + " doubles of scratch, the fixed "
                         "maximum is " + std::to_string(kNoallocScratchDoubles) +
                         " (8*npts*nt + ceil(npts/max(1,32/ncopies))*window); use fwh_integrate").c_str());
     double* X = nullptr;
-    const int rc = noalloc_scratch(&X);
+    rc = noalloc_scratch(&X);
     if (rc != FR_OK) return rc;
-    double* partial = X + size_t(npts) * NSER * nt;
-    const int64_t nw = int64_t(nt) * npts;
-    k_fwh_series<<<unsigned((nw + 255) / 256), 256, 0, s>>>(hist, nt, npts, n, k, X);
-    const size_t sm = FWH_SH_BYTES * size_t(group) * ncopies;
-    cudaError_t err = cudaGetLastError();
-    if (err == cudaSuccess && sm > 48 * 1024)
-        err = cudaFuncSetAttribute(k_fwh_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    for (int o = 0; o < nobs && err == cudaSuccess; ++o) {
-        dim3 grid(unsigned(ngroups), unsigned((Tn[o] + 128 * FWH_KO - 1) / (128 * FWH_KO)));
-        k_fwh_accum<<<grid, 128, sm, s>>>(X, nt, npts, y, dS, k, obs[o * 3 + 0], obs[o * 3 + 1], obs[o * 3 + 2],
-                                          tstart[o], Tn[o], ncopies, Lspan, group, partial);
-        k_fwh_reduce<<<unsigned((Tn[o] + 31) / 32), dim3(32, 32), 0, s>>>(partial, ngroups, Tn[o],
-                                                                          p_out + size_t(o) * cap);
-        err = cudaGetLastError();
-        nt_out[o] = Tn[o];
-        t0_out[o] = tstart[o];
-    }
-    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-    if (err != cudaSuccess) return fr_set_error_from_fwh(FR_ECUDA, cudaGetErrorString(err));
-    return FR_OK;
+    return fwh_run(pl, hist, nt, npts, y, n, dS, obs, nobs, Lspan, ncopies, p_out, cap, nt_out, t0_out, X,
+                   X + fwh_series_doubles(npts, nt), s);
 }

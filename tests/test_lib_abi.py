@@ -111,3 +111,31 @@ def test_new_entry_points_reject_bad_input_on_host(lib):
     assert lib.fr_set_adaptive_dt(None, 0.5) == F.FR_EINVAL
     assert lib.fr_cand_dt(None, 0, C.byref(t)) == F.FR_EINVAL
     assert lib.fr_set_element_order(None, -1, None) == F.FR_EINVAL
+
+
+def _function_body(src, name):
+    """Source text of the first definition of function `name` (brace matched)."""
+    import re
+    m = re.search(r"\b%s\s*\([^;{]*\)\s*\{" % re.escape(name), src)
+    assert m, name
+    i, depth = m.end() - 1, 0
+    for j in range(i, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        if depth == 0:
+            return src[i:j + 1]
+    raise AssertionError(name)
+
+
+def test_noalloc_fwh_path_names_no_device_allocation():
+    # fwh_integrate_noalloc and every helper it calls use no allocating
+    # runtime routine; fwh_integrate, which shares the helpers, does
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2501_05709_gb300", "csrc", "fwh.cu")).read()
+    body = _function_body(src, "fwh_integrate_noalloc")
+    called = {"fwh_plan", "fwh_run", "noalloc_scratch", "fwh_series_doubles", "fwh_partial_doubles"}
+    assert called <= set(re.findall(r"\b(\w+)\s*\(", body))
+    alloc = re.compile(r"\b(cudaMalloc\w*|cudaFree\w*|cudaMallocAsync|cudaFreeAsync|cuMem\w*Alloc\w*|malloc|new)\b")
+    for name in ["fwh_integrate_noalloc"] + sorted(called):
+        assert not alloc.search(_function_body(src, name)), name
+    assert re.search(r"\bcudaMalloc\b", _function_body(src, "fwh_integrate"))
