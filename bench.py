@@ -15,6 +15,11 @@ is reported beside it, with the FP32 state deviation from FP64 after the
 timed steps.  `--gpus N` under torchrun runs N independent replicas (the path
 does not need a collective); value = all replicas' work / max time.
 
+After the headline workload the same measurement runs on the batched poll
+(12 NACA candidates of uneven meshes in one context, mixed precision, each at
+its own time step) and is reported under "batched", with its FP64 path and the
+per-candidate mean C_L / C_D of both precisions.
+
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload (the only other place this script runs it) and prints its line.
 """
@@ -342,8 +347,8 @@ def gpu_leg(args, rank, world, local_rank):
     meshes, opts, state_of, surfaces, curved, dts = build_workload(args.workload)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
-    prec = F.FR_FP32 if args.precision == "fp32" else F.FR_FP64
-    rsz = 4 if prec == F.FR_FP32 else 8
+    prec = {"fp32": F.FR_FP32, "tf32": F.FR_TF32_TC, "bf16x3": F.FR_BF16X3_TC, "fp64": F.FR_FP64}[args.precision]
+    rsz = 8 if prec == F.FR_FP64 else 4
     ctx = F.fr_mesh_load(meshes, opts(prec))
     for k, d in enumerate(dts or []):
         F.fr_set_cand_dt(ctx, k, d)
@@ -397,7 +402,8 @@ def gpu_leg(args, rank, world, local_rank):
     ck = clocks.stop() if clocks else None
     value = replica_throughput(dof * 4 * args.steps, ms / 1e3, world)
 
-    # per-kernel durations of the same steps, events around each launch
+    # per-kernel durations over as many further steps, inside graph replay
+    # (one step captured with an event record node around every kernel)
     kms, kn = F.fr_profile_step(ctx, args.steps, sh)
     hbm, peak_kind = peaks()
     ab = algorithmic_bytes(E, p, rsz, viscous=viscous, curved=curved)
@@ -415,6 +421,10 @@ def gpu_leg(args, rank, world, local_rank):
                                             degrees=np.bincount(orders, minlength=p + 1).tolist())
     u32 = F.fr_state_get(ctx)
     steps_done = args.warmup + 2 * args.steps
+    # per-candidate wall forces accumulated over the same steps (C_L, C_D,
+    # mean C_L, mean C_D, steps)
+    walls = args.workload.startswith(("naca", "batch"))
+    forces32 = [F.fr_forces(ctx, k) for k in range(ctx.ncand)] if walls else None
 
     # end to end through the C-ABI: pinned host state in, step, KE integral out
     host = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
@@ -439,7 +449,7 @@ def gpu_leg(args, rank, world, local_rank):
 
     # FP64 path, same workload, same number of steps
     fp64 = None
-    if not args.no_fp64 and prec == F.FR_FP32:
+    if not args.no_fp64 and prec != F.FR_FP64:
         c64 = F.fr_mesh_load(meshes, opts(F.FR_FP64))
         for k, d in enumerate(dts or []):
             F.fr_set_cand_dt(c64, k, d)
@@ -472,9 +482,17 @@ def gpu_leg(args, rank, world, local_rank):
         u64 = F.fr_state_get(c64)
         dev = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
         ke = F.fr_integrals(c64)[-1]
+        forces64 = [F.fr_forces(c64, k) for k in range(c64.ncand)] if forces32 is not None else None
         c64.close()
         fp64 = {"value": replica_throughput(dof * 4 * args.steps, ms64 / 1e3, world), "unit": UNIT, "ms_per_step": ms64 / args.steps,
                 "fp32_state_rel_l2_vs_fp64": dev, "steps_compared": steps_done, "ke_fp64": ke}
+        if forces32 is not None:
+            per = [{"cl_mean_fp64": f64[2], "cl_mean_fp32": f32[2], "cd_mean_fp64": f64[3], "cd_mean_fp32": f32[3]}
+                   for f32, f64 in zip(forces32, forces64)]
+            fp64["per_candidate_forces"] = per
+            fp64["max_abs_dev_cl_mean"] = max(abs(d["cl_mean_fp32"] - d["cl_mean_fp64"]) for d in per)
+            fp64["max_abs_dev_cd_mean"] = max(abs(d["cd_mean_fp32"] - d["cd_mean_fp64"]) for d in per)
+            fp64["force_steps"] = int(forces64[0][4])
         # FP64 kernels are bound by the FP64 pipe: executed FP64 flops per
         # launch (ncu: 2 DFMA + DADD + DMUL, stage average) against the DFMA
         # rate measured on this GPU
@@ -569,12 +587,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwh", action="store_true", help="skip the FW-H/PSD post-processing timing")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 12-candidate leg (timed after the headline workload)")
     ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
     ap.add_argument("--sponge", action="store_true",
                     help="O-grid workloads: degree p near the body down to 0 at the far field (4c/6c/8c)")
     ap.add_argument("--workload", default="tgv32_p3", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
-                    help="precision of the timed path (fp32 also times fp64 beside it)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3", "fp64"],
+                    help="precision of the timed path (fp32; tf32 / bf16x3: fp32 with the residual's line "
+                         "operators on the tensor cores; the reduced modes also time fp64 beside them)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -604,6 +625,20 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     r = gpu_leg(args, rank, world, local_rank)
+    batched = None
+    if not args.no_batched and args.workload != "batch12_p3":
+        bargs = argparse.Namespace(**vars(args))
+        bargs.workload, bargs.sponge, bargs.tile = "batch12_p3", False, 0
+        rb = gpu_leg(bargs, rank, world, local_rank)
+        batched = {"workload": "batch12_p3", "description": WORKLOADS["batch12_p3"], "value": rb["value"],
+                   "unit": UNIT, "ms_per_step": rb["ms"] / args.steps, "steps": args.steps, "warmup": args.warmup,
+                   "dtype": {"fp32": "f32", "tf32": "f32+tf32-tc", "bf16x3": "f32+bf16x3-tc", "fp64": "f64"}[args.precision], "elements": rb["elements"],
+                   "dof_per_variable": rb["dof"], "autotuned_elements_per_block": rb["tile_epb"],
+                   "gpu_launches": rb["launches"], "clocks": rb["clocks"], "roofline": rb["roofline"],
+                   "kernels": rb["kernels"], "e2e": rb["e2e"], "fp64": rb["fp64"],
+                   "note": "the FW-H window at an observer 10c away needs ~0.6 convective times, far more than "
+                           "these steps cover; OASPL mixed vs FP64 per candidate comes from the batched precision "
+                           "study (cases.py batch-precision)"}
     fwh = None
     if rank == 0 and not args.no_fwh:
         try:
@@ -629,9 +664,10 @@ def main():
         config["dof_per_variable"] = r["dof"]
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "f32+tf32-tc", "bf16x3": "f32+bf16x3-tc", "fp64": "f64"}[args.precision],
                 "data": "synthetic", "config": config, "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
-                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all, "fwh": fwh}
+                "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all,
+                "batched": batched, "fwh": fwh}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

@@ -59,6 +59,13 @@ extern "C" {
 #define FR_FP32 1        /* state and arithmetic in float; metrics computed in
                             double and rounded once; force, energy and FW-H
                             accumulators in double */
+#define FR_TF32_TC 2     /* FR_FP32 with the gradient and divergence line
+                            operators of the residual on the tensor cores,
+                            operands rounded to TF32, FP32 accumulation
+                            (3D, p = 3 or 4) */
+#define FR_BF16X3_TC 3   /* as FR_TF32_TC with each operand split into two
+                            bfloat16 parts (hi + lo) and three products
+                            (hi hi + hi lo + lo hi), FP32 accumulation */
 
 #define FR_CORR_DG 0       /* g_L = right Radau polynomial of degree p+1 */
 #define FR_CORR_HUYNH_G2 1 /* Huynh's g2 */
@@ -88,7 +95,7 @@ typedef struct {
 typedef struct {
     int order;          /* p, 1..4 */
     int correction;     /* FR_CORR_* */
-    int precision;      /* FR_FP64 or FR_FP32 */
+    int precision;      /* FR_FP64, FR_FP32, FR_TF32_TC or FR_BF16X3_TC */
     int viscous;        /* 0: Euler, 1: Navier-Stokes (BR2) */
     double gamma;       /* ratio of specific heats (1.4 in Section 2.1) */
     double prandtl;     /* Pr (0.71 in Section 2.1) */
@@ -133,21 +140,55 @@ int fr_cand_range(const fr_ctx* ctx, int cand, int64_t* first, int64_t* count);
 
 /* State upload / download in the canonical layout as double.  cand < 0
  * addresses the whole batch.  on_device != 0: u is a device pointer.
- * fr_state_set also resets the RK stage buffers and projects elements of
- * reduced degree (fr_set_element_order).  The call synchronises the given
- * stream before returning. */
+ * fr_state_set also resets the RK stage buffers, projects elements of
+ * reduced degree (fr_set_element_order) and clears the addressed candidates'
+ * non-finite flags (fr_nonfinite).  fr_state_get copies the state and then
+ * returns FR_ENONFINITE when an addressed candidate's flag is set (or, for a
+ * host copy, when a copied value is NaN or Inf).  Both calls synchronise the
+ * given stream before returning. */
 int fr_state_set(fr_ctx* ctx, int cand, const double* u, int on_device, void* stream);
 int fr_state_get(fr_ctx* ctx, int cand, double* u, int on_device, void* stream);
 
+/* Non-finite detection on the device: the last stage of every step tests each
+ * new state value (exponent bits all ones: NaN or infinity) and sets a flag
+ * for the element's candidate, so one diverging candidate of a batch does not
+ * hide behind the others.  *flag = 1 when candidate cand's flag (cand = -1:
+ * any candidate's) is set, else 0.  Flags stay set until fr_state_set.
+ * Synchronises the device.  Errors: FR_EINVAL. */
+int fr_nonfinite(const fr_ctx* ctx, int cand, int* flag);
+
+/* Explicit time integrator in coefficient form (Section 3.1 integrates with
+ * an optimal explicit scheme whose coefficients are given in the work it
+ * cites, not in the paper; this call takes any scheme that fits the form).
+ * Stage i = 1..nstages of a step from u0 with input v (v = u0 at stage 1)
+ * and k = R(v) at time t_n + tau_i dt:
+ *   acc <- e_i acc + f_i dt k                    (acc = 0 before stage 1)
+ *   v   <- a_i u0 + b_i v + c_i dt k + d_i acc   (rounded as ((a u0 + d acc)
+ *                                                 + b v) + (c dt) k, one FMA
+ *                                                 per step)
+ * and the last v is the new state.  coef: host [nstages][6] doubles
+ * (a, b, c, d, e, f).  This covers classic RK4 (stage i: (1,0,1/2,0,0,1/6),
+ * (1,0,1/2,0,1,1/3), (1,0,1,0,1,1/3), (1,0,1/6,1,1,0), which reproduces the
+ * built-in RK4 bit for bit), Shu-Osher SSP forms (d = e = f = 0) and 2N
+ * low-storage forms (a = c = 0, b = 1).  The stage times tau_i (for the
+ * energy source) are the scheme's own values on du/dt = 1.  nstages = 0
+ * returns to the built-in RK4.  Forces and surface samples are taken at the
+ * start of each step as before.  Errors: FR_EINVAL (nstages outside 0..16,
+ * non-finite coefficients, or a scheme whose step on du/dt = 1 does not
+ * advance u by dt), FR_ENOMEM (odd stage counts need a third trace buffer).
+ * Rebuilds the step's CUDA graph on its next replay. */
+int fr_set_rk_scheme(fr_ctx* ctx, int nstages, const double* coef);
+
 /* fr_residual (Eq. 1 semi-discretised: du/dt = R(u)): one residual evaluation
  * of the whole batch.  u and R are device pointers in the context precision
- * (double for FR_FP64, float for FR_FP32), canonical layout, E*nvar*Nsp
+ * (double for FR_FP64, float otherwise), canonical layout, E*nvar*Nsp
  * values each; they must not overlap.  Uses the context's trace buffers, so
  * calls on one context must not run concurrently. */
 int fr_residual(fr_ctx* ctx, const void* u, void* R, void* stream);
 
 /* fr_rk_step: advances the internal state by nsteps classic RK4 steps of
- * size dt (each step: 4 residual evaluations fused with the stage update),
+ * size dt (each step: 4 residual evaluations fused with the stage update;
+ * fr_set_rk_scheme selects another explicit scheme),
  * accumulating the wall force every step and appending one record to every
  * registered FW-H surface every step.  Enqueued on stream; returns without
  * synchronising. */
@@ -219,7 +260,9 @@ int fr_rk_step_graph(fr_ctx* ctx, int nsteps, void* stream);
 /* fr_forces (Section 3.2 mean lift and drag): out[0] = C_L and out[1] = C_D
  * of the last accumulated step, out[2] = mean C_L, out[3] = mean C_D over
  * the accumulated steps, out[4] = number of steps.  Synchronises the
- * context's work.  fr_forces_reset zeroes the running means. */
+ * context's work.  Returns FR_ENONFINITE (out still filled) when the
+ * candidate's non-finite flag is set.  fr_forces_reset zeroes the running
+ * means. */
 int fr_forces(fr_ctx* ctx, int cand, double out[5]);
 int fr_forces_reset(fr_ctx* ctx);
 
@@ -315,7 +358,8 @@ int fwh_psd(const double* p, int nobs, int nt, int ld, double dt, int nseg, doub
             int* nfreq_out, void* stream);
 
 /* Elements per thread block used by the residual kernels (0 = built-in
- * default); fr_autotune times the candidates on the current state and keeps
+ * default; 1..32, or 1..15 in 3D at p = 4, where two warps share each
+ * element); fr_autotune times the candidates on the current state and keeps
  * the fastest per kernel, returning it in *best. */
 int fr_set_tile(fr_ctx* ctx, int elems_per_block);
 int fr_autotune(fr_ctx* ctx, int* best);
@@ -330,11 +374,13 @@ int fr_probe_fp64_peak(double* gflops, void* stream);
  * benchmarking claims). */
 int64_t fr_launch_count(const fr_ctx* ctx);
 
-/* Measurement aid: runs nsteps RK4 steps without a graph on stream with a
- * CUDA event around every launch and returns the summed device time (ms)
- * per kernel kind in ms_out[0..5] = traces, viscous faces, residual+RK,
- * forces/sampling, energy source, reduced-degree projection, and their launch
- * counts in n_out[0..5].  Advances the state exactly like fr_rk_step. */
+/* Measurement aid: captures one RK4 step as a CUDA graph with an event
+ * record node around every kernel (the launch sequence of fr_rk_step_graph),
+ * replays it nsteps times on stream (synchronising after each replay to read
+ * the events) and returns the summed device time (ms) per kernel kind in
+ * ms_out[0..5] = traces, viscous faces, residual+RK, forces/sampling, energy
+ * source, reduced-degree projection, and their launch counts in n_out[0..5].
+ * Advances the state exactly like fr_rk_step. */
 int fr_profile_step(fr_ctx* ctx, int nsteps, void* stream, double ms_out[6], int64_t n_out[6]);
 
 #ifdef __cplusplus

@@ -215,6 +215,37 @@ class FRSolver:
         return u + dt * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
 
     # -------------------------------------------------------------------
+    @staticmethod
+    def coef_stage_times(coef):
+        """Stage abscissae tau_i of a scheme in coefficient form: the value of
+        stage i's input when the scheme integrates du/dt = 1 from u = 0 with
+        dt = 1 (so u equals the time), and the value reached after the step."""
+        v, acc, taus = 0.0, 0.0, []
+        for i, (a, b, c, d, e, f) in enumerate(np.asarray(coef, float).reshape(-1, 6)):
+            taus.append(v)
+            acc = (0.0 if i == 0 else e * acc) + f
+            v = a * 0.0 + b * v + c + d * acc
+        return np.array(taus), v
+
+    def coef_step(self, u, dt, coef, t=0.0):
+        """One step of an explicit scheme given in coefficient form (the reading
+        taken for the optimal explicit integrator that Section 3.1 uses and
+        whose coefficients are in the cited work): with u0 = u, v = u,
+        acc = 0, for each stage (a, b, c, d, e, f):
+            k = R(v, t + tau_i dt)
+            acc = e acc + f dt k      (acc = f dt k at the first stage)
+            v = a u0 + b v + c dt k + d acc
+        and the new state is the last v."""
+        coef = np.asarray(coef, float).reshape(-1, 6)
+        taus, _ = self.coef_stage_times(coef)
+        u0, v, acc = u, u, None
+        for i, (a, b, c, d, e, f) in enumerate(coef):
+            k = self.residual(v, t=t + taus[i] * dt)
+            acc = f * dt * k if i == 0 else e * acc + f * dt * k
+            v = a * u0 + b * v + c * dt * k + d * acc
+        return v
+
+    # -------------------------------------------------------------------
     def wall_force(self, u):
         """Force of the fluid on the walls, sum over wall face points of
         w_fp (p N - tau(G).N) with N the element's outward area-weighted

@@ -195,6 +195,135 @@ def precision_study(steps=25000, dt=4e-5, sample_every=4, n_theta=60, n_r=20, n_
     return out
 
 
+def batch_precision_study(n=12, seed=1, coarsen=4, n_z=2, first_cell=2e-2, steps=25000, dt=4e-5, sample_every=4,
+                          ncopies=1, observer=(1.0, -10.0, 0.1)):
+    """Per-candidate mean C_L, mean C_D and OASPL of a batched poll in FP32 and
+    in FP64: the n seeded sections of the batched workload (``batch_params``)
+    on O-grids coarsened by ``coarsen`` in both in-plane directions (uneven
+    sizes kept), all candidates in one context, steps*dt convective times (long
+    enough for a non-empty FW-H window at the observer 10c below the trailing
+    edge), the surface sampled every ``sample_every`` steps and ``ncopies``
+    spanwise copies in the FW-H integral."""
+    import torch
+    params = batch_params(n, seed)
+    meshes = []
+    for prm in params:
+        nt, nr = max(8, round(prm["n_theta"] / coarsen)), max(6, round(prm["n_r"] / coarsen))
+        nodes, conn = W.ogrid_mesh(nt, nr, n_z, 0.2, first_cell=first_cell, body="naca", naca=prm["naca"])
+        meshes.append((nodes, conn))
+    surface = W.cylinder_surface(radius=1.5, center=(0.5, 0.0), spacing=0.01, span=0.2)
+    res = {"candidates": [{"naca": list(prm["naca"]), "elements": len(m[0])} for prm, m in zip(params, meshes)],
+           "steps": steps, "dt": dt, "sample_every": sample_every, "ncopies": ncopies, "observer": list(observer)}
+    for prec, name in ((F.FR_FP32, "fp32"), (F.FR_FP64, "fp64")):
+        opts, free = naca_options(precision=prec, dt=dt)
+        rho, vel, p = free
+        with F.fr_mesh_load(meshes, opts) as ctx:
+            us = [W.perturbed_uniform(len(nd), ctx.nsp, rho, vel, p, amplitude=0.01, seed=k)
+                  for k, (nd, _) in enumerate(meshes)]
+            F.fr_state_set(ctx, np.concatenate(us))
+            cap = (steps + sample_every - 1) // sample_every
+            hs = [F.fwh_register(ctx, k, surface[0], cap, sample_every) for k in range(n)]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            F.fr_rk_step_graph(ctx, steps)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t
+            forces = [F.fr_forces(ctx, k) for k in range(n)]
+            hists = [F.fwh_history(ctx, h, len(surface[0])) for h in hs]
+            final = F.fr_state_get(ctx)
+            dof = ctx.nelem * ctx.nsp
+        c0 = math.sqrt(GAMMA * p / rho)
+        out = []
+        for k in range(n):
+            r = {"cl_mean": forces[k][2], "cd_mean": forces[k][3]}
+            try:
+                _, pp, prms, oaspl = oaspl_from_history(hists[k], surface, dt * sample_every, observer, free,
+                                                        np.asarray(vel) / c0, 0.2, ncopies)
+                r.update(oaspl_db=oaspl, prms=prms, window=len(pp))
+            except F.FrError as e:
+                r.update(oaspl_db=None, prms=None, window=0, fwh_error=str(e))
+            out.append(r)
+        res[name] = {"per_candidate": out, "seconds": secs, "dof": dof, "dof_stages_per_s": dof * 4 * steps / secs,
+                     "finite": bool(np.isfinite(final).all())}
+        res[name + "_state"] = final
+    a, b = res.pop("fp64_state"), res.pop("fp32_state")
+    res["fp32_state_rel_l2_vs_fp64"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    dev = []
+    for k in range(n):
+        d = {}
+        for key in ("cl_mean", "cd_mean", "oaspl_db"):
+            x, y = res["fp64"]["per_candidate"][k].get(key), res["fp32"]["per_candidate"][k].get(key)
+            if x is not None and y is not None:
+                d[key] = {"fp64": x, "fp32": y, "abs_dev": abs(y - x)}
+        dev.append(d)
+    res["deviation"] = dev
+    for key in ("cl_mean", "cd_mean", "oaspl_db"):
+        v = [d[key]["abs_dev"] for d in dev if key in d]
+        if v:
+            res["max_abs_dev_" + key] = max(v)
+    return res
+
+
+def precision_modes_study(order=4, n=32, steps=200, dt=1.5e-4, mach=0.1, modes=("fp32", "tf32", "bf16x3")):
+    """Taylor-Green vortex (Re 1600) on the periodic n^3 box at FR order p in
+    FP64 and in each reduced mode (fp32; tf32 / bf16x3: fp32 with the
+    residual's gradient and divergence line operators on the tensor cores):
+    the kinetic-energy history over `steps` RK4 steps (every step), its
+    dissipation rate -dKE/dt (central differences), the residual of the
+    initial state and the final state, each against the FP64 run, and the
+    graph-replayed time per step of every mode."""
+    import torch
+    nodes, conn = W.box_mesh(3, n, 0.0, 2 * math.pi, q=1)
+    p_inf = 1.0 / (GAMMA * mach ** 2)
+    prec = {"fp64": F.FR_FP64, "fp32": F.FR_FP32, "tf32": F.FR_TF32_TC, "bf16x3": F.FR_BF16X3_TC}
+    runs = {}
+    for name in ("fp64",) + tuple(modes):
+        opts = F.options(order=order, precision=prec[name], viscous=True, mu=1.0 / 1600.0, p_inf=p_inf, dt=dt)
+        with F.fr_mesh_load((nodes, conn), opts) as ctx:
+            u0 = np.ascontiguousarray(np.moveaxis(W.taylor_green(F.fr_sp_coords(ctx), mach=mach), 0, 1))
+            dtype = torch.float64 if name == "fp64" else torch.float32
+            ud = torch.tensor(u0, dtype=dtype, device="cuda")
+            Rd = torch.empty_like(ud)
+            F.fr_residual(ctx, ud, Rd)
+            torch.cuda.synchronize()
+            R = Rd.double().cpu().numpy()
+            del ud, Rd
+            F.fr_state_set(ctx, u0)
+            ke = [F.fr_integrals(ctx)[-1]]
+            for _ in range(steps):
+                F.fr_rk_step_graph(ctx, 1)
+                ke.append(F.fr_integrals(ctx)[-1])
+            final = F.fr_state_get(ctx)
+            F.fr_state_set(ctx, u0)
+            F.fr_rk_step_graph(ctx, 3)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            F.fr_rk_step_graph(ctx, 20)
+            b.record()
+            torch.cuda.synchronize()
+            runs[name] = {"ke": np.array(ke), "R": R, "final": final, "ms_per_step": a.elapsed_time(b) / 20,
+                          "dof": ctx.nelem * ctx.nsp}
+    ref = runs["fp64"]
+    eps = -np.gradient(ref["ke"], dt)
+    out = {"order": order, "n": n, "steps": steps, "dt": dt, "dof": ref["dof"],
+           "fp64": {"ms_per_step": ref["ms_per_step"], "ke_final": float(ref["ke"][-1]),
+                    "dissipation_final": float(eps[-1])}}
+    for name in modes:
+        r = runs[name]
+        e = -np.gradient(r["ke"], dt)
+        out[name] = {
+            "ms_per_step": r["ms_per_step"],
+            "dof_stages_per_s": r["dof"] * 4 / (r["ms_per_step"] / 1e3),
+            "residual_rel_l2_vs_fp64": float(np.linalg.norm(r["R"] - ref["R"]) / np.linalg.norm(ref["R"])),
+            "final_state_rel_l2_vs_fp64": float(np.linalg.norm(r["final"] - ref["final"]) /
+                                                np.linalg.norm(ref["final"])),
+            "ke_max_rel_dev": float(np.max(np.abs(r["ke"] - ref["ke"]) / ref["ke"])),
+            "dissipation_max_rel_dev": float(np.max(np.abs(e - eps)) / np.max(np.abs(eps))),
+        }
+    return out
+
+
 # ---------------------------------------------------------------- Section 3.4: the optimisation loop
 def design_mesh(X, n_theta=60, n_r=20, n_z=2, span=0.2, r_outer=10.0, first_cell=2e-2, pivot=(0.25, 0.0)):
     """O-grid of the design X = [c_max %, position of c_max (tenths), t_max %,
@@ -240,11 +369,24 @@ def evaluate_designs(designs, steps=25000, dt=4e-5, sample_every=4, precision=F.
         hs = [F.fwh_register(ctx, k, surface[0], cap, sample_every) for k in range(len(meshes))]
         F.fr_rk_step_graph(ctx, steps)
         torch.cuda.synchronize()
-        forces = [F.fr_forces(ctx, k) for k in range(len(meshes))]
+        forces = []
+        for k in range(len(meshes)):
+            # a candidate whose run diverged (device non-finite flag) has no
+            # forces; the others of the batch keep theirs
+            try:
+                forces.append(F.fr_forces(ctx, k))
+            except F.FrError as e:
+                if e.code != F.FR_ENONFINITE:
+                    raise
+                forces.append(None)
         hists = [F.fwh_history(ctx, h, len(surface[0])) for h in hs]
     c0 = math.sqrt(GAMMA * p / rho)
     mach_vec = np.asarray(vel) / c0
     for k, X in enumerate(designs):
+        if forces[k] is None:
+            out.append({"design": np.asarray(X, float), "cl_mean": None, "cd_mean": None, "oaspl_db": None,
+                        "prms": None, "nonfinite": True})
+            continue
         r = {"design": np.asarray(X, float), "cl_mean": forces[k][2], "cd_mean": forces[k][3]}
         observer = (tes[k][0], tes[k][1] - 10.0, 0.5 * span)
         try:
@@ -367,6 +509,10 @@ if __name__ == "__main__":
     import sys
     if len(sys.argv) > 1 and sys.argv[1] == "naca-precision":
         print(json.dumps(precision_study(), default=float))
+    elif len(sys.argv) > 1 and sys.argv[1] == "precision-modes":
+        print(json.dumps(precision_modes_study(order=int(sys.argv[2]) if len(sys.argv) > 2 else 4), default=float))
+    elif len(sys.argv) > 1 and sys.argv[1] == "batch-precision":
+        print(json.dumps(batch_precision_study(), default=float))
     elif len(sys.argv) > 1 and sys.argv[1] == "monopole-box":
         res = {}
         for order in (1, 2, 3):
@@ -383,4 +529,5 @@ if __name__ == "__main__":
                           "history": [{k: v for k, v in h.items()} for h in res.history]},
                          default=lambda a: np.asarray(a).tolist()))
     else:
-        print("usage: python -m paper_2501_05709_gb300.cases naca-precision|monopole-box|optimize [iterations]")
+        print("usage: python -m paper_2501_05709_gb300.cases "
+              "naca-precision|batch-precision|precision-modes [order]|monopole-box|optimize [iterations]")

@@ -100,6 +100,14 @@ struct fr_ctx {
     int sp_n = 0;                             // capped elements (0: none)
     int32_t *sp_elem = nullptr, *sp_cap = nullptr;  // device [sp_n]
     std::vector<int> sp_off;                  // [ncand + 1]: each candidate's slice of the list
+    // non-finite state detection: nonfinite[c] != 0 once candidate c's state
+    // held a NaN or an infinity at the end of a step (cleared by fr_state_set)
+    int* nonfinite = nullptr;                 // device [ncand]
+    // explicit scheme in coefficient form (empty: classic RK4), per stage
+    // (a, b, c, d, e, f); ls_time[i] = abscissa of stage i's input (in dt)
+    std::vector<std::array<double, 6>> lsc;
+    std::vector<double> ls_time;
+    void* ufb3 = nullptr;                     // third trace buffer (odd stage counts)
 };
 
 namespace {
@@ -276,6 +284,11 @@ int L_resid(fr_ctx* c, const Real* u, const Real* uf, const frk::Stage<Real>& st
     const auto ph = phys_of<Real>(c);
     const auto g = geo_of<Real>(c);
     ++c->launches;
+    if constexpr (sizeof(Real) == 4) {
+        if (c->prec >= FR_TF32_TC)
+            return frl::residual_tc3(c->p, c->prec == FR_TF32_TC ? 1 : 2, u, uf, fvn, c->E, op, ph, g, st, c->lc[2],
+                                     s);
+    }
     return c->dim == 2 ? frl::residual<Real, 2>(c->p, u, uf, fvn, c->E, op, ph, g, st, c->lc[2], s)
                        : frl::residual<Real, 3>(c->p, u, uf, fvn, c->E, op, ph, g, st, c->lc[2], s);
 }
@@ -308,22 +321,29 @@ int L_sample(fr_ctx* c, Surface& sf, cudaStream_t s) {
                                               static_cast<Real*>(sf.hist), sf.count, sf.cap, sf.every, s);
 }
 
-// Optional per-launch event pairs for fr_profile_step: kind 0..5.
+// Optional per-launch event pairs for fr_profile_step: kind 0..5.  With
+// `external` set the records are made during stream capture and become event
+// record nodes of the graph (re-recorded at every replay).
 struct Prof {
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind;
     cudaStream_t s = nullptr;
+    bool external = false;
+    void record(cudaEvent_t e) {
+        if (external) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
+    }
     void mark_begin(int k) {
         cudaEvent_t a;
         cudaEventCreate(&a);
-        cudaEventRecord(a, s);
+        record(a);
         ev.push_back(a);
         kind.push_back(k);
     }
     void mark_end() {
         cudaEvent_t b;
         cudaEventCreate(&b);
-        cudaEventRecord(b, s);
+        record(b);
         ev.push_back(b);
     }
 };
@@ -368,10 +388,20 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         const int rc = enqueue_adaptive_dt<Real>(c, s);
         if (rc) return rc;
     }
-    for (int stage = 1; stage <= 4; ++stage) {
+    // stage s reads the traces of its input and writes those of its output;
+    // the step ends with the traces of the new u0 in ufb[0].  Even stage
+    // counts alternate ufb[1], ufb[0]; odd ones alternate ufb[1], ufb3 and end
+    // in ufb[0].
+    const int ns = c->lsc.empty() ? 4 : int(c->lsc.size());
+    auto trace_buf = [&](int st) -> Real* {
+        if (st == 0 || st == ns) return static_cast<Real*>(c->ufb[0]);
+        if (ns % 2 == 0) return static_cast<Real*>(c->ufb[st & 1]);
+        return static_cast<Real*>(st & 1 ? c->ufb[1] : c->ufb3);
+    };
+    for (int stage = 1; stage <= ns; ++stage) {
         const Real* in = (stage == 1) ? u0 : us;
-        const Real* uf_in = static_cast<const Real*>(c->ufb[(stage - 1) & 1]);
-        Real* uf_out = static_cast<Real*>(c->ufb[stage & 1]);
+        const Real* uf_in = trace_buf(stage - 1);
+        Real* uf_out = trace_buf(stage);
         int rc;
         if (c->visc) {
             if (pr) pr->mark_begin(1);
@@ -398,19 +428,35 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         st.us = us;
         st.acc = acc;
         st.uf_next = uf_out;
+        st.nonfinite = c->nonfinite;
+        st.cand_off = c->cand_off_d;
+        st.ncand = c->ncand;
+        double cfac = stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5;
+        if (!c->lsc.empty()) {
+            const auto& k = c->lsc[stage - 1];
+            st.ls = 1;
+            st.last = stage == ns;
+            st.ca = Real(k[0]);
+            st.cb = Real(k[1]);
+            st.cc = Real(k[2]);
+            st.cd = Real(k[3]);
+            st.ce = Real(k[4]);
+            st.cf = Real(k[5]);
+            cfac = c->ls_time[stage - 1];
+        }
         if (pr) pr->mark_begin(2);
         rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
         if (c->src_nentry > 0) {
             if (pr) pr->mark_begin(4);
-            rc = L_source<Real>(c, src_of<Real>(c, stage == 1 ? 0.0 : stage == 4 ? 1.0 : 0.5), st, s);
+            rc = L_source<Real>(c, src_of<Real>(c, cfac), st, s);
             if (pr) pr->mark_end();
             CKL(rc, "source kernel");
         }
         if (c->sp_n > 0) {
             if (pr) pr->mark_begin(5);
-            rc = stage == 4 ? L_sponge<Real>(c, u0, nullptr, uf_out, s) : L_sponge<Real>(c, us, acc, uf_out, s);
+            rc = stage == ns ? L_sponge<Real>(c, u0, nullptr, uf_out, s) : L_sponge<Real>(c, us, acc, uf_out, s);
             if (pr) pr->mark_end();
             CKL(rc, "sponge kernel");
         }
@@ -489,6 +535,15 @@ int orient_map(int dim, int np, int o, int fp) {
 
 size_t smem_of(const fr_ctx* c, int kernel, int epb);
 
+// threads per element of the element kernels, and the most elements a block
+// may hold (1024 threads; at 64 threads per element, 15 named barriers)
+int tpe_of(const fr_ctx* c) {
+    if (c->prec == FR_FP64)
+        return c->dim == 2 ? frl::threads_per_element<double, 2>(c->p) : frl::threads_per_element<double, 3>(c->p);
+    return c->dim == 2 ? frl::threads_per_element<float, 2>(c->p) : frl::threads_per_element<float, 3>(c->p);
+}
+int max_epb(const fr_ctx* c) { return tpe_of(c) == 64 ? 15 : 32; }
+
 // default: 8 warps (elements) per block, fewer when a block would need more
 // than 96 KB of shared memory
 void default_launch(fr_ctx* c) {
@@ -496,7 +551,7 @@ void default_launch(fr_ctx* c) {
         int epb = 8;
         while (epb > 1 && smem_of(c, k, epb) > 96 * 1024) epb /= 2;
         c->lc[k].epb = epb;
-        c->lc[k].threads = 32 * epb;
+        c->lc[k].threads = tpe_of(c) * epb;
     }
 }
 
@@ -513,7 +568,7 @@ void release(fr_ctx* c) {
     void* bufs[] = {c->u0, c->us, c->acc, c->ufb[0], c->ufb[1], c->fvn, c->S, c->J, c->iJ, c->N, c->nbr,
                     c->wall_ef, c->wall_off_d, c->fnow, c->fsum, c->fcnt, c->partial, c->stage64, c->dte,
                     c->fpart, c->src_elem, c->src_cand, c->src_w, c->src_A, c->src_f, c->tnow, c->dtc,
-                    c->hlen, c->cand_off_d, c->lam, c->sp_elem, c->sp_cap};
+                    c->hlen, c->cand_off_d, c->lam, c->sp_elem, c->sp_cap, c->nonfinite, c->ufb3};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& s : c->surf) {
@@ -559,7 +614,9 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
     const int dim = m[0].dim;
     if (dim != 2 && dim != 3) return fail(FR_EINVAL, "dim must be 2 or 3");
     if (o->order < 1 || o->order > 4) return fail(FR_EINVAL, "order must be 1..4");
-    if (o->precision != FR_FP64 && o->precision != FR_FP32) return fail(FR_EINVAL, "bad precision");
+    if (o->precision < FR_FP64 || o->precision > FR_BF16X3_TC) return fail(FR_EINVAL, "bad precision");
+    if (o->precision >= FR_TF32_TC && (dim != 3 || o->order < 3))
+        return fail(FR_EINVAL, "the tensor-core precision modes are built for 3D at p = 3 and 4");
     if (o->correction != FR_CORR_DG && o->correction != FR_CORR_HUYNH_G2) return fail(FR_EINVAL, "bad correction");
     if (!(o->gamma > 1.0) || !(o->prandtl > 0.0) || o->mu < 0.0 || !(o->rho_inf > 0.0) || !(o->p_inf > 0.0))
         return fail(FR_EINVAL, "bad gas or free-stream constants");
@@ -856,6 +913,12 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
     cudaMemset(c->fnow, 0, sizeof(double) * 3 * ncand);
     cudaMemset(c->fsum, 0, sizeof(double) * 3 * ncand);
     cudaMemset(c->fcnt, 0, sizeof(double) * ncand);
+    if (cudaMalloc(&c->nonfinite, sizeof(int) * ncand) != cudaSuccess) {
+        c->nonfinite = nullptr;
+        release(c);
+        return fail(FR_ENOMEM, "cudaMalloc failed for the non-finite flags");
+    }
+    cudaMemset(c->nonfinite, 0, sizeof(int) * ncand);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         release(c);
         return fail(FR_ECUDA, "cannot create a stream");
@@ -941,6 +1004,7 @@ extern "C" int fr_state_set(fr_ctx* c, int cand, const double* u, int on_device,
     const int64_t n = count * c->nv * c->nsp;
     char* dst = static_cast<char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
     c->traces_valid = false;
+    CK(cudaMemsetAsync(c->nonfinite + (cand < 0 ? 0 : cand), 0, sizeof(int) * (cand < 0 ? c->ncand : 1), s));
     if (c->prec == FR_FP64) {
         CK(cudaMemcpyAsync(dst, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     } else if (on_device) {
@@ -998,6 +1062,62 @@ extern "C" int fr_state_get(fr_ctx* c, int cand, double* u, int on_device, void*
         for (int64_t i = 0; i < n; ++i)
             if (!std::isfinite(u[i])) return fail(FR_ENONFINITE, "state holds NaN or Inf");
     }
+    // flags set on the device by the last stage of a step
+    for (int k = (cand < 0 ? 0 : cand); k < (cand < 0 ? c->ncand : cand + 1); ++k) {
+        int bad = 0;
+        CK(cudaMemcpy(&bad, c->nonfinite + k, sizeof(int), cudaMemcpyDeviceToHost));
+        if (bad) return fail(FR_ENONFINITE, "candidate " + std::to_string(k) + ": a step produced NaN or Inf");
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_nonfinite(const fr_ctx* c, int cand, int* flag) {
+    if (!c || !flag || cand < -1 || cand >= c->ncand) return fail(FR_EINVAL, "bad argument");
+    CK(cudaDeviceSynchronize());
+    *flag = 0;
+    for (int k = (cand < 0 ? 0 : cand); k < (cand < 0 ? c->ncand : cand + 1); ++k) {
+        int bad = 0;
+        CK(cudaMemcpy(&bad, c->nonfinite + k, sizeof(int), cudaMemcpyDeviceToHost));
+        *flag |= bad ? 1 : 0;
+    }
+    return FR_OK;
+}
+
+extern "C" int fr_set_rk_scheme(fr_ctx* c, int nstages, const double* coef) {
+    if (!c || nstages < 0 || nstages > 16 || (nstages > 0 && !coef)) return fail(FR_EINVAL, "bad argument");
+    if (nstages == 0) {
+        c->lsc.clear();
+        c->ls_time.clear();
+        invalidate_graph(c);
+        return FR_OK;
+    }
+    std::vector<std::array<double, 6>> k(nstages);
+    for (int i = 0; i < nstages; ++i)
+        for (int j = 0; j < 6; ++j) {
+            k[i][j] = coef[i * 6 + j];
+            if (!std::isfinite(k[i][j])) return fail(FR_EINVAL, "non-finite scheme coefficient");
+        }
+    // stage abscissae from the scheme applied to du/dt = 1 (u = t, dt = 1):
+    // the value of each stage's input is its time; one step must reach 1
+    std::vector<double> tin(nstages);
+    double v = 0.0, acc = 0.0;
+    for (int i = 0; i < nstages; ++i) {
+        tin[i] = v;
+        acc = (i == 0 ? 0.0 : k[i][4] * acc) + k[i][5];
+        v = k[i][0] * 0.0 + k[i][1] * v + k[i][2] + k[i][3] * acc;
+    }
+    if (!(std::fabs(v - 1.0) <= 1e-12))
+        return fail(FR_EINVAL, "inconsistent scheme: one step of du/dt = 1 must advance u by dt");
+    if (nstages % 2 == 1 && nstages > 1 && !c->ufb3) {
+        const size_t ntrace = size_t(c->E) * c->nf * c->nv * c->nfp * c->rsz;
+        if (cudaMalloc(&c->ufb3, ntrace) != cudaSuccess) {
+            c->ufb3 = nullptr;
+            return fail(FR_ENOMEM, "cannot allocate the third trace buffer");
+        }
+    }
+    c->lsc = k;
+    c->ls_time = tin;
+    invalidate_graph(c);
     return FR_OK;
 }
 
@@ -1347,6 +1467,9 @@ extern "C" int fr_forces(fr_ctx* c, int cand, double out[5]) {
     out[2] = cnt > 0 ? ml / (qa * cnt) : 0.0;
     out[3] = cnt > 0 ? md / (qa * cnt) : 0.0;
     out[4] = cnt;
+    int bad = 0;
+    CK(cudaMemcpy(&bad, c->nonfinite + cand, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) return fail(FR_ENONFINITE, "candidate " + std::to_string(cand) + ": a step produced NaN or Inf");
     return FR_OK;
 }
 
@@ -1577,6 +1700,8 @@ extern "C" int fwh_clear(fr_ctx* c, int handle) {
 // ---------------------------------------------------------------- tiles
 extern "C" int fr_set_tile(fr_ctx* c, int epb) {
     if (!c || epb < 0 || epb > 32) return fail(FR_EINVAL, "bad tile (elements per block 0..32)");
+    if (epb > max_epb(c))
+        return fail(FR_EINVAL, "bad tile: at most " + std::to_string(max_epb(c)) + " elements per block at this order");
     if (epb == 0) {
         default_launch(c);
     } else {
@@ -1584,7 +1709,7 @@ extern "C" int fr_set_tile(fr_ctx* c, int epb) {
             if (smem_of(c, k, epb) > 227 * 1024) return fail(FR_EINVAL, "tile needs too much shared memory");
         for (int k = 0; k < 3; ++k) {
             c->lc[k].epb = epb;
-            c->lc[k].threads = 32 * epb;
+            c->lc[k].threads = tpe_of(c) * epb;
         }
     }
     invalidate_graph(c);
@@ -1608,8 +1733,9 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
     for (int epb : cand) {
         bool fits = true;
         for (int k = 0; k < 3; ++k) fits = fits && smem_of(c, k, epb) <= 200 * 1024;
+        fits = fits && epb <= max_epb(c);
         if (!fits) continue;
-        for (int k = 0; k < 3; ++k) c->lc[k] = frk::Launch{epb, 32 * epb};
+        for (int k = 0; k < 3; ++k) c->lc[k] = frk::Launch{epb, tpe_of(c) * epb};
         for (int kern = 0; kern < 3; ++kern) {
             if (kern == 1 && !c->visc) continue;
             float tot = 0;
@@ -1645,7 +1771,7 @@ extern "C" int fr_autotune(fr_ctx* c, int* best) {
             }
             if (rc == 0 && tot > 0 && tot < bestt[kern]) {
                 bestt[kern] = tot;
-                bestl[kern] = frk::Launch{epb, 32 * epb};
+                bestl[kern] = frk::Launch{epb, tpe_of(c) * epb};
             }
         }
     }
@@ -1703,24 +1829,58 @@ extern "C" int fr_probe_fp64_peak(double* gflops, void* stream) {
 
 extern "C" int fr_profile_step(fr_ctx* c, int nsteps, void* stream, double ms_out[6], int64_t n_out[6]) {
     if (!c || nsteps < 0 || !ms_out || !n_out) return fail(FR_EINVAL, "bad argument");
-    Prof pr;
-    pr.s = static_cast<cudaStream_t>(stream);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int k = 0; k < 6; ++k) {
         ms_out[k] = 0.0;
         n_out[k] = 0;
     }
-    int rc = c->prec == FR_FP64 ? ensure_traces<double>(c, pr.s, &pr) : ensure_traces<float>(c, pr.s, &pr);
-    for (int k = 0; k < nsteps && rc == FR_OK; ++k)
-        rc = c->prec == FR_FP64 ? enqueue_step<double>(c, pr.s, &pr) : enqueue_step<float>(c, pr.s, &pr);
-    cudaError_t e = cudaStreamSynchronize(pr.s);
-    for (size_t i = 0; i < pr.kind.size() && 2 * i + 1 < pr.ev.size(); ++i) {
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]);
-        ms_out[pr.kind[i]] += ms;
-        n_out[pr.kind[i]] += 1;
+    // traces of a state set from outside (outside the graph, as in fr_rk_step_graph)
+    {
+        Prof p0;
+        p0.s = s;
+        const int rc = c->prec == FR_FP64 ? ensure_traces<double>(c, s, &p0) : ensure_traces<float>(c, s, &p0);
+        CK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < p0.kind.size() && 2 * i + 1 < p0.ev.size(); ++i) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, p0.ev[2 * i], p0.ev[2 * i + 1]);
+            ms_out[p0.kind[i]] += ms;
+            n_out[p0.kind[i]] += 1;
+        }
+        for (auto ev : p0.ev) cudaEventDestroy(ev);
+        if (rc) return rc;
     }
+    // one step captured with event record nodes around every kernel, replayed
+    // nsteps times: the same launch sequence as fr_rk_step_graph
+    Prof pr;
+    pr.s = c->cap_stream;
+    pr.external = true;
+    const int64_t before = c->launches;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = c->prec == FR_FP64 ? enqueue_step<double>(c, c->cap_stream, &pr)
+                                      : enqueue_step<float>(c, c->cap_stream, &pr);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+    const int64_t per_step = c->launches - before;
+    c->launches = before;
+    cudaGraphExec_t gx = nullptr;
+    cudaError_t e = ec;
+    if (rc == FR_OK && ec == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int k = 0; k < nsteps && rc == FR_OK && e == cudaSuccess; ++k) {
+        e = cudaGraphLaunch(gx, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        c->launches += per_step;
+        for (size_t i = 0; i < pr.kind.size() && 2 * i + 1 < pr.ev.size(); ++i) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, pr.ev[2 * i], pr.ev[2 * i + 1]);
+            ms_out[pr.kind[i]] += ms;
+            n_out[pr.kind[i]] += 1;
+        }
+    }
+    if (gx) cudaGraphExecDestroy(gx);
     for (auto ev : pr.ev) cudaEventDestroy(ev);
     if (rc) return rc;
-    if (e != cudaSuccess) return fail(FR_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(FR_ECUDA, std::string("profile graph: ") + cudaGetErrorString(e));
     return FR_OK;
 }

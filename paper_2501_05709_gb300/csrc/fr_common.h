@@ -60,14 +60,21 @@ struct Geo {
     int bnd;
 };
 
-// RK4 stage control for the fused residual/update kernel.
+// Stage control for the fused residual/update kernel.  Classic RK4 (ls = 0):
 //   stage 0: write R only (fr_residual)
 //   stage 1: input u0;  acc = dt/6 k1;        us = u0 + dt/2 k1
 //   stage 2: input us;  acc += dt/3 k2;       us = u0 + dt/2 k2
 //   stage 3: input us;  acc += dt/3 k3;       us = u0 + dt k3
 //   stage 4: input us;  u0 = u0 + acc + dt/6 k4
-// uf_next (stages 1-4): traces of the stage's output state, for the next stage.
+// Coefficient form (ls = 1), stage i >= 1 with input v (u0 at stage 1, us
+// after) and k = R(v):
+//   acc <- e acc + f dt k          (acc taken as 0 at stage 1)
+//   out  = a u0 + b v + c dt k + d acc, evaluated as ((a u0 + d acc) + b v) + (c dt) k
+//   out -> us, or -> u0 at the last stage (acc is then not written)
+// uf_next (stages >= 1): traces of the stage's output state, for the next stage.
 // dte (optional): per-element time step overriding dt.
+// nonfinite (optional): the last stage sets nonfinite[c] when candidate c's
+// new state holds a NaN or an infinity (candidate offsets cand_off[0..ncand]).
 template <typename Real>
 struct Stage {
     int stage;
@@ -78,7 +85,26 @@ struct Stage {
     Real* us;
     Real* acc;
     Real* uf_next;
+    int* nonfinite = nullptr;
+    const int64_t* cand_off = nullptr;
+    int ncand = 0;
+    int ls = 0;       // 1: coefficient form
+    int last = 0;     // coefficient form: this stage writes u0
+    Real ca = 0, cb = 0, cc = 0, cd = 0, ce = 0, cf = 0;
 };
+
+// Bit test for NaN and infinity (exponent field all ones), independent of
+// fast-math flags.
+__host__ __device__ inline bool not_finite(float x) {
+    union { float f; uint32_t u; } b;
+    b.f = x;
+    return (b.u & 0x7f800000u) == 0x7f800000u;
+}
+__host__ __device__ inline bool not_finite(double x) {
+    union { double f; uint64_t u; } b;
+    b.f = x;
+    return (b.u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+}
 
 // Energy source of Appendix D, Eq. D.1,
 //   s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi f_m t),
@@ -168,6 +194,17 @@ int source_stage(int P, const frk::Src<Real>& src, const frk::Stage<Real>& st, c
 template <typename Real, int DIM>
 int cfl(int P, const Real* u, const Real* hlen, int64_t E, const int64_t* cand_off, int ncand,
         const frk::Phys<Real>& ph, unsigned long long* lam, void* stream);
+
+// residual of the tensor-core precision modes (3D, P = 3 or 4; opm 1: TF32,
+// 2: BF16x3), float data
+int residual_tc3(int P, int opm, const float* u, const float* uf, const float* fvn, int64_t E,
+                 const frk::Ops<float>& op, const frk::Phys<float>& ph, const frk::Geo<float>& g,
+                 const frk::Stage<float>& st, frk::Launch lc, void* stream);
+
+// threads per element of the element kernels (32 or 64; at 64 an element
+// group synchronises on a named barrier, so a block holds at most 15 groups)
+template <typename Real, int DIM>
+int threads_per_element(int P);
 
 // dynamic shared memory of kernel 0 (traces), 1 (viscous faces), 2 (residual);
 // curved meshes stage per-point metrics and need more

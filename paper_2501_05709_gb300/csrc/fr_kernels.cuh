@@ -19,6 +19,7 @@
 // BR2, metric terms S = |J| dxi/dx in conservative-curl form.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "fr_common.h"
@@ -33,6 +34,25 @@ struct Sz {
     static constexpr int NF = 2 * DIM;
     static constexpr int NV = DIM + 2;
 };
+
+// Threads per element of the element kernels (k_traces, k_visc_face,
+// k_residual): one warp, or two warps for p = 4 in 3D, whose 19 KB of shared
+// memory per element would otherwise leave 12 warps per SM to hide latency.
+// `lane` below is the thread's index within its element group (0..T-1) and
+// the phases of a group are separated by grp_sync (a named barrier per group
+// when T = 64; barrier 0 stays free).
+template <int DIM, int P>
+struct Grp {
+    static constexpr int T = (DIM == 3 && P == 4) ? 64 : 32;
+};
+template <int T>
+__device__ __forceinline__ void grp_sync(int grp) {
+    if constexpr (T == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;\n" ::"r"(grp + 1), "n"(T) : "memory");
+    }
+}
 
 // solution point j (along direction d) of the line through face point fp of a
 // face normal to d; face points enumerate the remaining directions in
@@ -273,6 +293,15 @@ __device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N,
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// explicitly rounded arithmetic of the stage updates, so that the classic RK4
+// update and the coefficient form with RK4's coefficients round identically
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 // Per-element (per-warp) shared-memory footprint of each kernel, in Reals.
 // Regions (Reals) of one warp's shared memory.  F = NF*NV*NFP is one
 // element's face data, U = NV*NSP its state.
@@ -413,14 +442,14 @@ __device__ __forceinline__ void vstore_line(Real* X, int v, int d, int ln, const
 // reference variable vref, whose shared offsets depend on the lane only (the
 // compiler keeps them out of the loop), in an array shifted by whole
 // variables (an even number of them, so the permuted placement is unchanged).
-template <int DIM, int P>
+template <int DIM, int P, int T = Grp<DIM, P>::T>
 struct LineTask {
     int t, v, ln, vref, shift;
     __device__ __forceinline__ LineTask(int lane, int it) {
         constexpr int NFP = Sz<DIM, P>::NFP, NSP = Sz<DIM, P>::NSP;
-        t = lane + 32 * it;
-        if constexpr (32 % NFP == 0 && (32 / NFP) % 2 == 0) {
-            constexpr int VPI = 32 / NFP;
+        t = lane + T * it;
+        if constexpr (T % NFP == 0 && (T / NFP) % 2 == 0) {
+            constexpr int VPI = T / NFP;
             vref = lane / NFP;
             ln = lane % NFP;
             v = vref + VPI * it;
@@ -480,6 +509,101 @@ __device__ __forceinline__ void ends_of(const Ops<Real>& op, const Real (&s)[NP]
     }
 }
 
+// ---- line operators on the tensor cores (precision modes FR_TF32_TC and
+// FR_BF16X3_TC of the residual kernel).  A pass over the lines of direction d
+// takes them 16 at a time as the rows of an m16n8k8 MMA: A[row][k] = point k
+// of the row's line (zero past NP), B[k][n] = D[n][k] for n < NP,
+// l_k(-1) for n = NP, l_k(+1) for n = NP + 1, zero beyond, so that one MMA
+// gives each line's derivative at its NP points and both of its end values,
+// accumulated in FP32.  OPM 1: operands rounded to TF32; OPM 2: each operand
+// split into two BF16 parts, hi + lo, and three MMAs (hi hi + hi lo + lo hi).
+// Fragments of m16n8k8 (g = lane / 4, t = lane % 4 within the warp): TF32 A
+// (g, t), (g+8, t), (g, t+4), (g+8, t+4), B (t, g), (t+4, g); BF16 A the
+// pairs (g, 2t..2t+1), (g+8, 2t..2t+1), B (2t..2t+1, g); C (g, 2t), (g, 2t+1),
+// (g+8, 2t), (g+8, 2t+1).
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void bf16_split(float x, unsigned short& hi, unsigned short& lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+}
+__device__ __forceinline__ uint32_t pack2(unsigned short a, unsigned short b) {
+    return uint32_t(a) | (uint32_t(b) << 16);
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// B[k][n] of the line-operator MMA (see above)
+template <int NP>
+__device__ __forceinline__ float tc_b(const Ops<float>& op, int k, int n) {
+    if (k >= NP) return 0.0f;
+    if (n < NP) return op.D[n * MAXNP + k];
+    if (n == NP) return op.lm[k];
+    if (n == NP + 1) return op.lm[NP - 1 - k];
+    return 0.0f;
+}
+
+// this thread's B fragment: TF32 {b0, b1}; BF16x3 {hi, lo}
+template <int NP, int OPM>
+__device__ __forceinline__ void tc_b_frag(const Ops<float>& op, int lw, uint32_t (&bf)[2]) {
+    const int g = lw >> 2, t = lw & 3;
+    if constexpr (OPM == 1) {
+        bf[0] = tf32_of(tc_b<NP>(op, t, g));
+        bf[1] = tf32_of(tc_b<NP>(op, t + 4, g));
+    } else {
+        unsigned short h0, l0, h1, l1;
+        bf16_split(tc_b<NP>(op, 2 * t, g), h0, l0);
+        bf16_split(tc_b<NP>(op, 2 * t + 1, g), h1, l1);
+        bf[0] = pack2(h0, h1);
+        bf[1] = pack2(l0, l1);
+    }
+}
+
+// C of one tile of 16 line tasks, rows r0 = t0 (this thread's g) and r1 = t0 + 8:
+// line task t of direction d is (variable vbase + t / NFP, line t % NFP) of X
+template <int DIM, int P, int OPM>
+__device__ __forceinline__ void tc_tile(const float* X, int vbase, int d, int t0, const uint32_t (&bf)[2], int lw,
+                                        float (&c)[4]) {
+    using VL = Vol<DIM, P, float>;
+    constexpr int NP = P + 1, NFP = Sz<DIM, P>::NFP, NL = Sz<DIM, P>::NV * NFP;
+    const int t = lw & 3, t1 = t0 + 8;
+    auto x = [&](int row, int k) -> float {
+        return (row < NL && k < NP) ? X[VL::line(vbase + row / NFP, d, row % NFP, k)] : 0.0f;
+    };
+    c[0] = c[1] = c[2] = c[3] = 0.0f;
+    if constexpr (OPM == 1) {
+        mma_tf32(c, tf32_of(x(t0, t)), tf32_of(x(t1, t)), tf32_of(x(t0, t + 4)), tf32_of(x(t1, t + 4)), bf[0],
+                 bf[1]);
+    } else {
+        unsigned short h00, l00, h01, l01, h10, l10, h11, l11;
+        bf16_split(x(t0, 2 * t), h00, l00);
+        bf16_split(x(t0, 2 * t + 1), h01, l01);
+        bf16_split(x(t1, 2 * t), h10, l10);
+        bf16_split(x(t1, 2 * t + 1), h11, l11);
+        const uint32_t ah0 = pack2(h00, h01), ah1 = pack2(h10, h11), al0 = pack2(l00, l01), al1 = pack2(l10, l11);
+        mma_bf16(c, al0, al1, bf[0]);   // small products first
+        mma_bf16(c, ah0, ah1, bf[1]);
+        mma_bf16(c, ah0, ah1, bf[0]);
+    }
+}
+
 // both end values of line ln (direction d) of variable v of volume array X:
 // m = sum_j l_j(-1) s_j and p = sum_j l_j(+1) s_j
 template <int DIM, int P, typename Real>
@@ -508,44 +632,44 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // copy N Reals g -> s across the warp; 16-byte chunks when VEC (both sides
 // 16-byte aligned and N*sizeof(Real) a multiple of 16), else element-wise
 template <int N, bool VEC, typename Real>
-__device__ __forceinline__ void warp_stage(Real* s, const Real* g, int lane) {
+__device__ __forceinline__ void warp_stage(Real* s, const Real* g, int lane, int T = 32) {
     if constexpr (VEC) {
         constexpr int NC = int(N * sizeof(Real) / 16);
         constexpr int RPC = int(16 / sizeof(Real));
-        for (int c = lane; c < NC; c += 32) cp_async16(s + c * RPC, g + c * RPC);
+        for (int c = lane; c < NC; c += T) cp_async16(s + c * RPC, g + c * RPC);
     } else {
-        for (int c = lane; c < N; c += 32) cp_async_small<int(sizeof(Real))>(s + c, g + c);
+        for (int c = lane; c < N; c += T) cp_async_small<int(sizeof(Real))>(s + c, g + c);
     }
 }
 
 // as warp_stage, choosing 16-byte chunks at run time when the shared side
 // allows them (SVEC) and the global address is 16-byte aligned
 template <int N, bool SVEC, typename Real>
-__device__ __forceinline__ void warp_stage_auto(Real* s, const Real* g, int lane) {
+__device__ __forceinline__ void warp_stage_auto(Real* s, const Real* g, int lane, int T = 32) {
     constexpr bool V = SVEC && (N * sizeof(Real)) % 16 == 0;
     if (V && (reinterpret_cast<uintptr_t>(g) & 15u) == 0)
-        warp_stage<N, V>(s, g, lane);
+        warp_stage<N, V>(s, g, lane, T);
     else
-        warp_stage<N, false>(s, g, lane);
+        warp_stage<N, false>(s, g, lane, T);
 }
 
 // stage one element's state [NV][NSP] (canonical global layout) into the
 // volume placement; rows go as 16-byte copies when the global rows are aligned
 template <int DIM, int P, typename Real>
-__device__ __forceinline__ void warp_stage_vol(Real* s, const Real* g, int lane) {
+__device__ __forceinline__ void warp_stage_vol(Real* s, const Real* g, int lane, int T = 32) {
     using V = Vol<DIM, P, Real>;
     constexpr int NV = DIM + 2, NP = P + 1, NSP = V::NSP;
     if constexpr (V::ROW4) {
         if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
             constexpr int NR = NV * NSP / NP;   // rows
-            for (int k = lane; k < NR; k += 32) {
+            for (int k = lane; k < NR; k += T) {
                 const int v = k / (NSP / NP), r = k % (NSP / NP);
                 cp_async16(s + V::at(v, 0, r % NP, r / NP), g + k * NP);
             }
             return;
         }
     }
-    for (int k = lane; k < NV * NSP; k += 32)
+    for (int k = lane; k < NV * NSP; k += T)
         cp_async_small<int(sizeof(Real))>(s + V::pt(k / NSP, k % NSP), g + k);
 }
 
@@ -595,19 +719,20 @@ __device__ __forceinline__ void traces_at(const Real* X, int d, int fp, const Re
 }
 
 // traces of the element state su at every flux point -> ufe [NF][NV][NFP]
-// (global or shared), one line per task producing both faces of direction d
-template <int DIM, int P, typename Real>
+// (global or shared), one line per task producing both faces of direction d,
+// by T threads (lane 0..T-1)
+template <int DIM, int P, int T, typename Real>
 __device__ __forceinline__ void warp_write_traces(const Real* su, Real* __restrict__ ufe, const Ops<Real>& op,
                                                   int lane) {
     using Z = Sz<DIM, P>;
     constexpr int NFP = Z::NFP, NV = Z::NV;
-    constexpr int NL = NV * NFP, NLI = (NL + 31) / 32;
+    constexpr int NL = NV * NFP, NLI = (NL + T - 1) / T;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NLI; ++it) {
-            const LineTask<DIM, P> tk(lane, it);
-            if (NL % 32 != 0 && tk.t >= NL) break;
+            const LineTask<DIM, P, T> tk(lane, it);
+            if (NL % T != 0 && tk.t >= NL) break;
             Real m, p;
             line_ends<DIM, P>(su + tk.shift, tk.vref, op, d, tk.ln, m, p);
             ufe[2 * d * NV * NFP + tk.t] = m;
@@ -622,17 +747,18 @@ template <int DIM, int P, typename Real>
 __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int64_t E,
                          const __grid_constant__ Ops<Real> op) {
     using Z = Sz<DIM, P>;
+    constexpr int T = Grp<DIM, P>::T;   // threads per element
     constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    const int warp = threadIdx.x / T, lane = threadIdx.x % T;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
     if (e >= E) return;
     Real* su = reinterpret_cast<Real*>(smem) + warp * Smem<DIM, P>::traces;
-    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
+    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane, T);
     cp_async_commit();
     cp_async_wait<0>();
-    __syncwarp();
-    warp_write_traces<DIM, P>(su, uf + e * NF * NV * NFP, op, lane);
+    grp_sync<T>(warp);
+    warp_write_traces<DIM, P, T>(su, uf + e * NF * NV * NFP, op, lane);
 }
 
 // Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
@@ -646,14 +772,15 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                             int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
                             const __grid_constant__ Geo<Real> g) {
     using Z = Sz<DIM, P>;
+    constexpr int T = Grp<DIM, P>::T;   // threads per element
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
-    constexpr int NSPW = (NSP + 31) / 32;           // solution points per lane
+    constexpr int NSPW = (NSP + T - 1) / T;           // solution points per lane
     constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
-    constexpr int NLI = (NL + 31) / 32;             // ... per lane
-    constexpr int NFI = (2 * NFP + 31) / 32;        // face points of one direction per lane
+    constexpr int NLI = (NL + T - 1) / T;             // ... per lane
+    constexpr int NFI = (2 * NFP + T - 1) / T;        // face points of one direction per lane
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    const int warp = threadIdx.x / T, lane = threadIdx.x % T;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
     if (e >= E) return;
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
@@ -668,7 +795,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     // face codes of this element, broadcast to every lane
     int codes[NF];
     {
-        const int mine = lane < NF ? g.nbr[e * NF + lane] : 0;
+        const int mine = (lane & 31) < NF ? g.nbr[e * NF + (lane & 31)] : 0;
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
@@ -679,29 +806,29 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                         (SM::visc_a * sizeof(Real)) % 16 == 0;
     constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0 &&
                         (SM::vC * sizeof(Real)) % 16 == 0;
-    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane);
+    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane, T);
     cp_async_commit();
-    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane);
+    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane, T);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
         if (!BND || codes[f] >= 0)
-            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
+            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
     cp_async_commit();
     if (curved) {
-        warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane);
+        warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane, T);
         warp_stage_auto<NSP, VW && ((SM::visc + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
-            sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane);
+            sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane, T);
     }
     cp_async_commit();
     cp_async_wait<1>();
-    __syncwarp();
+    grp_sync<T>(warp);
     // B: jumps per face point
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + 32 * it;
-            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
+            const int t = lane + T * it;
+            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
@@ -723,7 +850,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             for (int v = 0; v < NV; ++v) sj[(f * NV + v) * NFP + fp] = uc[v] - uL[v];
         }
     }
-    __syncwarp();  // the gradient below overwrites the staged neighbour traces
+    grp_sync<T>(warp);  // the gradient below overwrites the staged neighbour traces
     if constexpr (curved) {
         // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
@@ -731,7 +858,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 #pragma unroll
             for (int it = 0; it < NLI; ++it) {
                 const LineTask<DIM, P> tk(lane, it);
-                if (NL % 32 != 0 && tk.t >= NL) break;
+                if (NL % T != 0 && tk.t >= NL) break;
                 Real s[NP], q[NP];
                 vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
 #pragma unroll
@@ -741,12 +868,12 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             }
         }
         cp_async_wait<0>();
-        __syncwarp();
+        grp_sync<T>(warp);
         // C2: physical gradient (1/|J|) S^T q at each solution point, in place
 #pragma unroll
         for (int s = 0; s < NSPW; ++s) {
-            const int sp = lane + 32 * s;
-            if (NSP % 32 != 0 && sp >= NSP) break;
+            const int sp = lane + T * s;
+            if (NSP % T != 0 && sp >= NSP) break;
             Real q[DIM][NV];
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
@@ -791,7 +918,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + 32 * it;
+            const int t = lane + T * it;
             const int side = t >= NFP ? 1 : 0;
             if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
         }
@@ -804,7 +931,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     if constexpr (!curved) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = min(lane + 32 * it, 2 * NFP - 1);
+            const int t = min(lane + T * it, 2 * NFP - 1);
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int a = fp % NP, b = DIM == 3 ? fp / NP : 0;
@@ -818,14 +945,14 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             }
         }
     }
-    __syncwarp();
+    grp_sync<T>(warp);
     // D: lifted face gradient, viscous normal flux
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + 32 * it;
-            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
+            const int t = lane + T * it;
+            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
@@ -936,22 +1063,25 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
 // Sweep C: common fluxes, corrected gradient, flux divergence with the FR
 // correction, R = -(1/|J|)[...], the RK4 stage update and (for the stepping
 // stages) the traces of the updated state written for the next stage.  MP and
-// BND as for k_visc_face; VISC: Navier-Stokes (BR2 viscous terms) or Euler.
-template <int DIM, int P, typename Real, int MP, bool VISC, bool BND>
+// BND as for k_visc_face; VISC: Navier-Stokes (BR2 viscous terms) or Euler;
+// OPM: the gradient and divergence line operators as FP32 FMAs (0) or on the
+// tensor cores with TF32 (1) or BF16x3 (2) operands (float only).
+template <int DIM, int P, typename Real, int MP, bool VISC, bool BND, int OPM = 0>
 __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real* __restrict__ u, const Real* __restrict__ uf,
                            const Real* __restrict__ fvn, int64_t E, const __grid_constant__ Ops<Real> op,
                            const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g,
                            const __grid_constant__ Stage<Real> st) {
     using Z = Sz<DIM, P>;
+    constexpr int T = Grp<DIM, P>::T;   // threads per element
     constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
-    constexpr int NSPW = (NSP + 31) / 32;           // solution points per lane
+    constexpr int NSPW = (NSP + T - 1) / T;           // solution points per lane
     constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
-    constexpr int NLI = (NL + 31) / 32;             // ... per lane
-    constexpr int NFI = (2 * NFP + 31) / 32;        // face points of one direction per lane
+    constexpr int NLI = (NL + T - 1) / T;             // ... per lane
+    constexpr int NFI = (2 * NFP + T - 1) / T;        // face points of one direction per lane
     constexpr bool PREFETCH = NSPW <= 2;            // RK arrays held in registers
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    const int warp = threadIdx.x / T, lane = threadIdx.x % T;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
     if (e >= E) return;
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
@@ -970,24 +1100,24 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     const int64_t base = e * NV * NSP;
     int codes[NF];
     {
-        const int mine = lane < NF ? g.nbr[e * NF + lane] : 0;
+        const int mine = (lane & 31) < NF ? g.nbr[e * NF + (lane & 31)] : 0;
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
     }
     constexpr bool VW = (SM::resid * sizeof(Real)) % 16 == 0 && (SM::resid_c * sizeof(Real)) % 16 == 0;
     constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::rC * sizeof(Real)) % 16 == 0 &&
                         (SM::rD * sizeof(Real)) % 16 == 0 && (SM::rE * sizeof(Real)) % 16 == 0;
-    warp_stage_vol<DIM, P>(su, u + base, lane);
+    warp_stage_vol<DIM, P>(su, u + base, lane, T);
     cp_async_commit();
-    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane);
+    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane, T);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
         if (!BND || codes[f] >= 0) {
-            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane);
+            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
             if constexpr (VISC)
-                warp_stage<NV * NFP, VS>(sm + f * NV * NFP, fvn + int64_t(codes[f] >> 3) * NV * NFP, lane);
+                warp_stage<NV * NFP, VS>(sm + f * NV * NFP, fvn + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
         }
-    if constexpr (VISC) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane);
+    if constexpr (VISC) warp_stage<NF * NV * NFP, VS>(so, fvn + e * NF * NV * NFP, lane, T);
     cp_async_commit();
     // face normals of this lane's face points, and the RK stage arrays (needed
     // only at the end): issue their loads now
@@ -996,7 +1126,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + 32 * it;
+            const int t = lane + T * it;
             const int side = t >= NFP ? 1 : 0;
             if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
         }
@@ -1005,7 +1135,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
         if (st.stage >= 2) {
 #pragma unroll
             for (int s = 0; s < NSPW; ++s) {
-                const int sp = lane + 32 * s;
+                const int sp = lane + T * s;
                 if (sp < NSP)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
@@ -1016,14 +1146,14 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
         }
     }
     cp_async_wait<0>();
-    __syncwarp();
+    grp_sync<T>(warp);
     // B: common normal flux (Rusanov minus common viscous) and jumps
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + 32 * it;
-            if ((2 * NFP) % 32 != 0 && t >= 2 * NFP) break;
+            const int t = lane + T * it;
+            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
             const int side = t >= NFP ? 1 : 0;
             const int fp = t - side * NFP;
             const int f = 2 * d + side;
@@ -1064,24 +1194,52 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             }
         }
     }
-    __syncwarp();
+    grp_sync<T>(warp);
     // curved meshes: stage S and 1/|J| into region E (free after the face
     // phase); the copy overlaps the gradient pass
     if (curved) {
-        warp_stage_auto<DIM * DIM * NSP, VW && (SM::rE * sizeof(Real)) % 16 == 0>(sg, g.S + e * g.sS_e, lane);
+        warp_stage_auto<DIM * DIM * NSP, VW && (SM::rE * sizeof(Real)) % 16 == 0>(sg, g.S + e * g.sS_e, lane, T);
         warp_stage_auto<NSP, VW && ((SM::rE + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
-            sg + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane);
+            sg + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane, T);
         cp_async_commit();
     }
+    // tensor-core mode: this thread's B fragment of the line operators, and
+    // its place in the MMA tiles (warp wg of the element group, g, t)
+    static_assert(OPM == 0 || sizeof(Real) == 4, "tensor-core line operators take float data");
+    constexpr int NTILE = (NL + 15) / 16, NWG = T / 32;
+    const int lw = lane & 31, wg = lane >> 5, gq = lw >> 2, tq = lw & 3;
+    uint32_t bfr[2] = {0u, 0u};
+    if constexpr (OPM != 0) tc_b_frag<NP, OPM>(reinterpret_cast<const Ops<float>&>(op), lw, bfr);
     // C1 (viscous): corrected reference gradient along lines,
     // q_d = D_d u + nsign h_f (u_c - u_f) for the two faces normal to d
-    if constexpr (VISC) {
+    if constexpr (VISC && OPM != 0) {
+#pragma unroll 1
+        for (int d = 0; d < DIM; ++d)
+            for (int q = wg; q < NTILE; q += NWG) {
+                float c[4];
+                tc_tile<DIM, P, OPM>(reinterpret_cast<const float*>(su), 0, d, 16 * q + gq, bfr, lw, c);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int tt = 16 * q + gq + 8 * h;
+                    if (tt >= NL) continue;
+                    const int v = tt / NFP, ln = tt % NFP;
+                    const Real jL = sj[2 * d * NV * NFP + tt], jR = sj[(2 * d + 1) * NV * NFP + tt];
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const int n = 2 * tq + w;
+                        if (n >= NP) continue;
+                        sF[VL::line(d * NV + v, d, ln, n)] = c[2 * h + w] + op.hm[NP - 1 - n] * jR - op.hm[n] * jL;
+                    }
+                }
+            }
+    }
+    if constexpr (VISC && OPM == 0) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
 #pragma unroll
             for (int it = 0; it < NLI; ++it) {
                 const LineTask<DIM, P> tk(lane, it);
-                if (NL % 32 != 0 && tk.t >= NL) break;
+                if (NL % T != 0 && tk.t >= NL) break;
                 Real s[NP], q[NP];
                 vload_line<DIM, P>(su + tk.shift, tk.vref, d, tk.ln, s);
                 const Real jL = sj[2 * d * NV * NFP + tk.t];
@@ -1094,12 +1252,12 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
         }
     }
     if (curved) cp_async_wait<0>();
-    __syncwarp();
+    grp_sync<T>(warp);
     // C2: flux at solution points, F~_d = sum_i S[d][i] (F_inv - F_vis)_i
 #pragma unroll 1
     for (int s = 0; s < NSPW; ++s) {
-        const int sp = lane + 32 * s;
-        if (NSP % 32 != 0 && sp >= NSP) break;
+        const int sp = lane + T * s;
+        if (NSP % T != 0 && sp >= NSP) break;
         Real uu[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) uu[v] = su[VL::pt(v, sp)];
@@ -1196,16 +1354,50 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
                 }
         }
     }
-    __syncwarp();
+    grp_sync<T>(warp);
     // D+E: per line of direction d, the flux jumps at both ends,
     // Fc.N - nsign I_f[F~_d], and the divergence plus correction, accumulated
     // direction by direction
+    if constexpr (OPM != 0) {
+#pragma unroll 1
+        for (int d = 0; d < DIM; ++d) {
+            for (int q = wg; q < NTILE; q += NWG) {
+                float c[4];
+                tc_tile<DIM, P, OPM>(reinterpret_cast<const float*>(sF), d * NV, d, 16 * q + gq, bfr, lw, c);
+                // both end values of rows g and g + 8, from the lanes of the
+                // quad that hold columns NP and NP + 1
+                const int qb = lw & ~3;
+                const float m0 = __shfl_sync(0xffffffffu, NP % 2 == 0 ? c[0] : c[1], qb + NP / 2);
+                const float m1 = __shfl_sync(0xffffffffu, NP % 2 == 0 ? c[2] : c[3], qb + NP / 2);
+                const float p0 = __shfl_sync(0xffffffffu, (NP + 1) % 2 == 0 ? c[0] : c[1], qb + (NP + 1) / 2);
+                const float p1 = __shfl_sync(0xffffffffu, (NP + 1) % 2 == 0 ? c[2] : c[3], qb + (NP + 1) / 2);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int tt = 16 * q + gq + 8 * h;
+                    if (tt >= NL) continue;
+                    const int v = tt / NFP, ln = tt % NFP;
+                    const Real cL = sc[2 * d * NV * NFP + tt] + (h ? m1 : m0);
+                    const Real cR = sc[(2 * d + 1) * NV * NFP + tt] - (h ? p1 : p0);
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const int n = 2 * tq + w;
+                        if (n >= NP) continue;
+                        Real val = op.hm[n] * cL + op.hm[NP - 1 - n] * cR + c[2 * h + w];
+                        const int a = VL::line(v, d, ln, n);
+                        if (d > 0) val += sd[a];
+                        sd[a] = val;
+                    }
+                }
+            }
+            grp_sync<T>(warp);
+        }
+    } else {
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NLI; ++it) {
             const LineTask<DIM, P> tk(lane, it);
-            if (NL % 32 != 0 && tk.t >= NL) break;
+            if (NL % T != 0 && tk.t >= NL) break;
             Real s[NP];
             vload_line<DIM, P>(sF + tk.shift, d * NV + tk.vref, d, tk.ln, s);
             Real m, pp;
@@ -1224,73 +1416,126 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
             }
             vstore_line<DIM, P>(sd + tk.shift, tk.vref, d, tk.ln, val);
         }
-        __syncwarp();
+        grp_sync<T>(warp);
+    }
     }
     // F: residual and RK stage per solution point; the new stage state
     // replaces su for the traces
     const Real dt = st.dte ? st.dte[e] : st.dt;
+    bool bad = false;   // the last stage's new state holds a NaN or an infinity
+    // one loop over this lane's values per kind of stage (the stage is uniform
+    // over the launch, so only one loop body runs): upd(r, u, u0, acc, gi)
+    // stores the stage arrays and returns the new stage state
+    auto stage_loop = [&](auto upd) {
 #pragma unroll
-    for (int s = 0; s < NSPW; ++s) {
-        const int sp = lane + 32 * s;
-        if (NSP % 32 != 0 && sp >= NSP) break;
-        const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
+        for (int s = 0; s < NSPW; ++s) {
+            const int sp = lane + T * s;
+            if (NSP % T != 0 && sp >= NSP) break;
+            const Real iJ = curved ? sg[DIM * DIM * NSP + sp] : g.iJ[e * g.sJ_e];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const int k = VL::pt(v, sp);
-            const Real r = -sd[k] * iJ;
-            const int64_t gi = base + v * NSP + sp;
-            Real u0v = Real(0), accv = Real(0);
-            if (st.stage >= 2) {
-                if constexpr (PREFETCH) {
-                    u0v = pu0[s][v];
-                    accv = pacc[s][v];
-                } else {
-                    u0v = st.u0[gi];
-                    accv = st.acc[gi];
+            for (int v = 0; v < NV; ++v) {
+                const int k = VL::pt(v, sp);
+                const Real r = -sd[k] * iJ;
+                const int64_t gi = base + v * NSP + sp;
+                Real u0v = Real(0), accv = Real(0);
+                if (st.stage >= 2) {
+                    if constexpr (PREFETCH) {
+                        u0v = pu0[s][v];
+                        accv = pacc[s][v];
+                    } else {
+                        u0v = st.u0[gi];
+                        accv = st.acc[gi];
+                    }
                 }
+                su[k] = upd(r, su[k], u0v, accv, gi);
             }
-            Real nu;
-            switch (st.stage) {
-                case 0:
+        }
+    };
+    if (st.ls) {
+        // coefficient form (see Stage); at stage 1 the input is u0 and acc is 0
+        const Real fdt = st.cf * dt, cdt = st.cc * dt;
+        if (st.last) {
+            stage_loop([&](Real r, Real u, Real u0v, Real accv, int64_t gi) {
+                if (st.stage == 1) u0v = u;
+                const Real an = st.stage == 1 ? mul_rn(fdt, r) : fma_rn(fdt, r, mul_rn(st.ce, accv));
+                Real nu = fma_rn(st.cd, an, mul_rn(st.ca, u0v));
+                nu = fma_rn(cdt, r, fma_rn(st.cb, u, nu));
+                st.u0[gi] = nu;
+                bad = bad || not_finite(nu);
+                return nu;
+            });
+        } else {
+            stage_loop([&](Real r, Real u, Real u0v, Real accv, int64_t gi) {
+                if (st.stage == 1) u0v = u;
+                const Real an = st.stage == 1 ? mul_rn(fdt, r) : fma_rn(fdt, r, mul_rn(st.ce, accv));
+                Real nu = fma_rn(st.cd, an, mul_rn(st.ca, u0v));
+                nu = fma_rn(cdt, r, fma_rn(st.cb, u, nu));
+                st.acc[gi] = an;
+                st.us[gi] = nu;
+                return nu;
+            });
+        }
+    } else {
+        switch (st.stage) {
+            case 0:
+                stage_loop([&](Real r, Real u, Real, Real, int64_t gi) {
                     st.R[gi] = r;
-                    nu = su[k];
-                    break;
-                case 1:
-                    st.acc[gi] = (dt * Real(1.0 / 6.0)) * r;
-                    nu = su[k] + (dt * Real(0.5)) * r;
+                    return u;
+                });
+                break;
+            case 1:
+                stage_loop([&](Real r, Real u, Real, Real, int64_t gi) {
+                    st.acc[gi] = mul_rn(dt * Real(1.0 / 6.0), r);
+                    const Real nu = fma_rn(dt * Real(0.5), r, u);
                     st.us[gi] = nu;
-                    break;
-                case 2:
-                    st.acc[gi] = accv + (dt * Real(1.0 / 3.0)) * r;
-                    nu = u0v + (dt * Real(0.5)) * r;
+                    return nu;
+                });
+                break;
+            case 2:
+                stage_loop([&](Real r, Real, Real u0v, Real accv, int64_t gi) {
+                    st.acc[gi] = fma_rn(dt * Real(1.0 / 3.0), r, accv);
+                    const Real nu = fma_rn(dt * Real(0.5), r, u0v);
                     st.us[gi] = nu;
-                    break;
-                case 3:
-                    st.acc[gi] = accv + (dt * Real(1.0 / 3.0)) * r;
-                    nu = u0v + dt * r;
+                    return nu;
+                });
+                break;
+            case 3:
+                stage_loop([&](Real r, Real, Real u0v, Real accv, int64_t gi) {
+                    st.acc[gi] = fma_rn(dt * Real(1.0 / 3.0), r, accv);
+                    const Real nu = fma_rn(dt, r, u0v);
                     st.us[gi] = nu;
-                    break;
-                default:
-                    nu = u0v + accv + (dt * Real(1.0 / 6.0)) * r;
+                    return nu;
+                });
+                break;
+            default:
+                stage_loop([&](Real r, Real, Real u0v, Real accv, int64_t gi) {
+                    const Real nu = fma_rn(dt * Real(1.0 / 6.0), r, add_rn(u0v, accv));
                     st.u0[gi] = nu;
-                    break;
-            }
-            su[k] = nu;
+                    bad = bad || not_finite(nu);
+                    return nu;
+                });
+                break;
         }
     }
+    if (st.nonfinite && __any_sync(0xffffffffu, bad) && (lane & 31) == 0) {
+        int c = 0;
+        while (c + 1 < st.ncand && e >= st.cand_off[c + 1]) ++c;
+        atomicOr(st.nonfinite + c, 1);
+    }
     if (st.uf_next) {
-        __syncwarp();
-        warp_write_traces<DIM, P>(su, st.uf_next + e * NF * NV * NFP, op, lane);
+        grp_sync<T>(warp);
+        warp_write_traces<DIM, P, T>(su, st.uf_next + e * NF * NV * NFP, op, lane);
     }
 }
 
 // Energy source of Appendix D (Eq. D.1), applied after the residual kernel of
 // a stage to the few elements that carry one (warp per source entry).  The
-// RK4 update is linear in the residual, so adding the source's share to the
+// stage update is linear in the residual, so adding the source's share to the
 // stage arrays afterwards equals adding it to R first: stage 0 adds s to R;
-// stages 1-4 add (dt/2, dt/2, dt, dt/6) s to the stage output (us, us, us,
-// u0) and (dt/6, dt/3, dt/3, -) s to acc, and, traces being linear in the
-// state, add the face traces of the state increment to the next traces.
+// RK4 stages 1-4 add (dt/2, dt/2, dt, dt/6) s to the stage output (us, us,
+// us, u0) and (dt/6, dt/3, dt/3, -) s to acc (the coefficient form: (c + d f)
+// dt s and f dt s); the element's next traces are then rewritten from its
+// updated stage output.
 template <int DIM, int P, typename Real>
 __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __grid_constant__ Stage<Real> st,
                                const __grid_constant__ Ops<Real> op) {
@@ -1301,7 +1546,7 @@ __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __gr
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + warp;
     if (j >= src.nentry) return;
-    Real* sdel = reinterpret_cast<Real*>(smem) + warp * NSP;   // state increment [sp] (volume placement)
+    Real* sst = reinterpret_cast<Real*>(smem) + warp * NV * NSP;   // updated element state (volume placement)
     const int64_t e = src.elem[j];
     const int c = src.cand[j];
     const double dt = double(st.dte ? st.dte[e] : st.dt);
@@ -1312,8 +1557,12 @@ __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __gr
         const double a = src.A[c * MAXSRC + m];
         amp[m] = a != 0.0 ? a * sinpi(2.0 * src.f[c * MAXSRC + m] * t) : 0.0;
     }
-    const double cs = st.stage == 3 ? dt : st.stage == 4 ? dt / 6.0 : 0.5 * dt;   // into the stage output
-    const double ca = st.stage == 1 ? dt / 6.0 : dt / 3.0;                       // into acc (stages 1-3)
+    // share of the source in the stage output and in acc: classic RK4, or the
+    // coefficient form (acc gains f dt s, the output (c + d f) dt s)
+    const bool last = st.ls ? st.last != 0 : st.stage == 4;
+    const double cs = st.ls ? (double(st.cc) + double(st.cd) * double(st.cf)) * dt
+                            : st.stage == 3 ? dt : st.stage == 4 ? dt / 6.0 : 0.5 * dt;
+    const double ca = st.ls ? double(st.cf) * dt : st.stage == 1 ? dt / 6.0 : dt / 3.0;
     const int64_t gbase = (e * NV + (NV - 1)) * NSP;                             // energy row
     for (int sp = lane; sp < NSP; sp += 32) {
         double sv = 0.0;
@@ -1324,25 +1573,30 @@ __global__ void k_source_stage(const __grid_constant__ Src<Real> src, const __gr
             continue;
         }
         const Real du = Real(cs * sv);
-        if (st.stage == 4) {
+        if (last) {
             st.u0[gbase + sp] += du;
         } else {
             st.us[gbase + sp] += du;
             st.acc[gbase + sp] += Real(ca * sv);
         }
-        sdel[VL::pt(0, sp)] = du;
     }
     if (st.stage == 0 || !st.uf_next) return;
     __syncwarp();
-    // traces of the increment (one variable) added to the energy rows of the next traces
+    // the next traces of this element, rewritten from its updated state with
+    // the same line-end arithmetic as every other element's, so that traces
+    // always equal the traces of the state (a state set from outside gets the
+    // same values bit for bit)
+    const Real* out = (last ? st.u0 : st.us) + e * NV * NSP;
+    for (int k = lane; k < NV * NSP; k += 32) sst[VL::pt(k / NSP, k % NSP)] = out[k];
+    __syncwarp();
     Real* uf = st.uf_next + e * NF * NV * NFP;
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
-        for (int ln = lane; ln < NFP; ln += 32) {
+        for (int t = lane; t < NV * NFP; t += 32) {
             Real m, p;
-            line_ends<DIM, P>(sdel, 0, op, d, ln, m, p);
-            uf[(2 * d * NV + NV - 1) * NFP + ln] += m;
-            uf[((2 * d + 1) * NV + NV - 1) * NFP + ln] += p;
+            line_ends<DIM, P>(sst, t / NFP, op, d, t % NFP, m, p);
+            uf[2 * d * NV * NFP + t] = m;
+            uf[(2 * d + 1) * NV * NFP + t] = p;
         }
 }
 
@@ -1406,7 +1660,7 @@ __global__ void k_sponge(const __grid_constant__ Sponge<Real> sp, Real* __restri
         Real* be = b + e * NV * NSP;
         for (int k = lane; k < NV * NSP; k += 32) be[k] = sb[VL::pt(k / NSP, k % NSP)];
     }
-    if (uf_out) warp_write_traces<DIM, P>(sa, uf_out + e * NF * NV * NFP, op, lane);
+    if (uf_out) warp_write_traces<DIM, P, 32>(sa, uf_out + e * NF * NV * NFP, op, lane);
 }
 
 // Adaptive time step (Section 3.1: adaptive time stepping): per element

@@ -31,7 +31,7 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& 
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, E, op);
+    k<<<grid_of(E, lc.epb), frk::Grp<FR_DIM, P>::T * lc.epb, sm, s>>>(u, uf, E, op);
     return int(cudaGetLastError());
 }
 
@@ -47,7 +47,7 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g);
+    k<<<grid_of(E, lc.epb), frk::Grp<FR_DIM, P>::T * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g);
     return int(cudaGetLastError());
 }
 
@@ -61,7 +61,7 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), 32 * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g, st);
+    k<<<grid_of(E, lc.epb), frk::Grp<FR_DIM, P>::T * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g, st);
     return int(cudaGetLastError());
 }
 
@@ -116,6 +116,17 @@ int residual<FR_REAL, FR_DIM>(int P, const FR_REAL* u, const FR_REAL* uf, const 
 #undef C
 #undef R
 #undef B
+}
+
+template <>
+int threads_per_element<FR_REAL, FR_DIM>(int P) {
+    switch (P) {
+        case 1: return frk::Grp<FR_DIM, 1>::T;
+        case 2: return frk::Grp<FR_DIM, 2>::T;
+        case 3: return frk::Grp<FR_DIM, 3>::T;
+        case 4: return frk::Grp<FR_DIM, 4>::T;
+        default: return 32;
+    }
 }
 
 template <>
@@ -180,7 +191,7 @@ int source_stage<FR_REAL, FR_DIM>(int P, const frk::Src<FR_REAL>& src, const frk
     if (src.nentry <= 0) return 0;
     const unsigned blocks = unsigned((src.nentry + 3) / 4);
 #define C(PP) (frk::k_source_stage<FR_DIM, PP, FR_REAL><<<blocks, 128,                                    \
-                   4 * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(src, st, op),                   \
+                   4 * frk::Sz<FR_DIM, PP>::NV * frk::Sz<FR_DIM, PP>::NSP * sizeof(FR_REAL), s>>>(src, st, op),                   \
                int(cudaGetLastError()))
     FR_DISPATCH(C)
 #undef C

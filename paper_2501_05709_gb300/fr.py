@@ -26,6 +26,8 @@ FR_EWINDOW = -6
 FR_EMESH = -7
 FR_FP64 = 0
 FR_FP32 = 1
+FR_TF32_TC = 2
+FR_BF16X3_TC = 3
 FR_CORR_DG = 0
 FR_CORR_HUYNH_G2 = 1
 FR_BC_WALL = 1
@@ -71,6 +73,8 @@ _SIGS = {
     "fr_set_cand_dt": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "fr_forces": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_forces_reset": (C.c_int, [C.c_void_p]),
+    "fr_nonfinite": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "fr_set_rk_scheme": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fr_integrals": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fwh_register": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "fwh_sample": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -269,6 +273,23 @@ def fr_forces(ctx, cand=0):
 
 def fr_forces_reset(ctx):
     _check(lib().fr_forces_reset(ctx.handle))
+
+
+def fr_nonfinite(ctx, cand=-1):
+    """True when a step left NaN or Inf in candidate cand (-1: any)."""
+    f = C.c_int(0)
+    _check(lib().fr_nonfinite(ctx.handle, cand, C.byref(f)))
+    return bool(f.value)
+
+
+def fr_set_rk_scheme(ctx, coef=None):
+    """Explicit scheme in coefficient form, coef [nstages][6] = (a, b, c, d, e,
+    f) per stage (see include/fr.h); None returns to the built-in RK4."""
+    if coef is None:
+        _check(lib().fr_set_rk_scheme(ctx.handle, 0, None))
+        return
+    k = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1, 6)
+    _check(lib().fr_set_rk_scheme(ctx.handle, len(k), _ptr(k)))
 
 
 def fr_integrals(ctx, cand=-1):
