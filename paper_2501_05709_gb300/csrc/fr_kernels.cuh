@@ -192,6 +192,48 @@ __device__ __forceinline__ void visc_flux(const Real* u, const Real (*G)[DIM], R
     }
 }
 
+// The same viscous flux contracted with a vector N, F_vis(u, G).N, without
+// forming the tensor: (tau N)_i = mu sum_j (dV_i/dx_j + dV_j/dx_i) N_j
+// - (2/3) mu div V N_i and the energy entry V.(tau N) - q.N.
+template <int DIM, typename Real>
+__device__ __forceinline__ void visc_flux_n(const Real* u, const Real (*G)[DIM], Real mu, Real kappa, const Real* N,
+                                            Real* Fn) {
+    constexpr int NV = DIM + 2;
+    const Real ir = Real(1) / u[0];
+    Real V[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) V[i] = u[1 + i] * ir;
+    Real gV[DIM][DIM];
+    Real gn = Real(0);
+    const Real Er = u[NV - 1] * ir;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        Real s = (G[NV - 1][j] - Er * G[0][j]) * ir;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            gV[i][j] = (G[1 + i][j] - V[i] * G[0][j]) * ir;
+            s -= V[i] * gV[i][j];
+        }
+        gn += s * N[j];
+    }
+    Real div = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) div += gV[i][i];
+    const Real c23 = Real(2.0 / 3.0) * mu * div;
+    Real en = Real(0);
+    Fn[0] = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        Real a = Real(0);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) a += (gV[i][j] + gV[j][i]) * N[j];
+        const Real tn = mu * a - c23 * N[i];
+        Fn[1 + i] = tn;
+        en += V[i] * tn;
+    }
+    Fn[NV - 1] = en + kappa * gn;
+}
+
 // Boundary states: ghost for the inviscid flux and common solution u_b.
 template <int DIM, typename Real>
 __device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N, const Phys<Real>& ph,
@@ -387,15 +429,21 @@ struct Vol {
             return v * NSP + i0 + NP * (i1 + NP * i2);
         }
     }
-    // point sp = i0 + NP i1 (+ NP^2 i2) of variable v
+    // point sp = i0 + NP i1 (+ NP^2 i2) of variable v (in the plain placement
+    // simply v NSP + sp, written so that no division by NP is left)
     __device__ __forceinline__ static int pt(int v, int sp) {
-        if constexpr (DIM == 2) return v * NSP + sp;
+        if constexpr (DIM == 2 || !SWZ) return v * NSP + sp;
         else return at(v, sp % NP, (sp / NP) % NP, sp / (NP * NP));
     }
-    // point j of the line through face point ln in direction d (see line_sp)
+    // point j of the line through face point ln in direction d (see line_sp);
+    // in the plain placement lines along xi_0 and xi_2 need no division by NP
     __device__ __forceinline__ static int line(int v, int d, int ln, int j) {
         if constexpr (DIM == 2) {
             return v * NSP + line_sp<DIM, NP>(d, ln, j);
+        } else if constexpr (!SWZ) {
+            if (d == 0) return v * NSP + NP * ln + j;
+            if (d == 2) return v * NSP + ln + NP * NP * j;
+            return v * NSP + ln % NP + NP * (j + NP * (ln / NP));
         } else {
             const int a = ln % NP, b = ln / NP;
             if (d == 0) return at(v, j, a, b);
@@ -463,22 +511,27 @@ struct LineTask {
     }
 };
 
-// q[i] += sum_j D[i][j] s[j].  For p = 3 in FP32 the four rows go as two
-// packed pairs (two FP32 FMAs per instruction, the same order of operations).
+// q[i] += sum_j D[i][j] s[j].  In FP32 the rows go as packed pairs (two FP32
+// FMAs per instruction, the same order of operations), an odd last row alone.
 template <int NP, typename Real>
 __device__ __forceinline__ void apply_D(const Ops<Real>& op, const Real (&s)[NP], Real (&q)[NP]) {
-    if constexpr (NP == 4 && sizeof(Real) == 4) {
-        float2 a = make_float2(q[0], q[1]), b = make_float2(q[2], q[3]);
+    if constexpr (sizeof(Real) == 4) {
+        float2 a[NP / 2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int r = 0; r < NP / 2; ++r) a[r] = make_float2(q[2 * r], q[2 * r + 1]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
             const float2 sj = make_float2(s[j], s[j]);
-            a = __ffma2_rn(make_float2(op.D[0 * MAXNP + j], op.D[1 * MAXNP + j]), sj, a);
-            b = __ffma2_rn(make_float2(op.D[2 * MAXNP + j], op.D[3 * MAXNP + j]), sj, b);
+#pragma unroll
+            for (int r = 0; r < NP / 2; ++r)
+                a[r] = __ffma2_rn(make_float2(op.D[(2 * r) * MAXNP + j], op.D[(2 * r + 1) * MAXNP + j]), sj, a[r]);
+            if constexpr (NP % 2 == 1) q[NP - 1] += op.D[(NP - 1) * MAXNP + j] * s[j];
         }
-        q[0] = a.x;
-        q[1] = a.y;
-        q[2] = b.x;
-        q[3] = b.y;
+#pragma unroll
+        for (int r = 0; r < NP / 2; ++r) {
+            q[2 * r] = a[r].x;
+            q[2 * r + 1] = a[r].y;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < NP; ++i)
@@ -768,7 +821,7 @@ __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int6
 // (affine), 2 affine with diagonal S (axis-aligned); BND false: the mesh has
 // no boundary faces (fully periodic), so the boundary-state code is left out.
 template <int DIM, int P, typename Real, int MP, bool BND>
-__global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
+__global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
                             int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
                             const __grid_constant__ Geo<Real> g) {
     using Z = Sz<DIM, P>;
@@ -822,6 +875,158 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
     cp_async_commit();
     cp_async_wait<1>();
     grp_sync<T>(warp);
+    if constexpr (!curved) {
+        // Affine elements, one pass per face point: the jump u_c - u_f, the
+        // lifted face gradient and the viscous normal flux, all in registers.
+        // With constant metrics the trace of (1/|J|) S^T D u is (1/|J|) S^T
+        // applied to the traces of the reference derivatives: along the face
+        // the derivatives of the face trace (interpolation to the face and
+        // differentiation along it commute), across it the derivative of the
+        // normal line at its end, sum_j l_j'(+-1) u_j.
+        // the normals of this lane's face points and the element's metrics:
+        // loads issued before the wait for the staged arrays
+        Real Nr[DIM][NFI][DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+            for (int it = 0; it < NFI; ++it) {
+                const int t = lane + T * it;
+                const int side = t >= NFP ? 1 : 0;
+                if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
+            }
+        Real S[DIM * DIM];
+        load_S<DIM>(g, e, 0, S);
+        const Real iJ = g.iJ[e * g.sJ_e];
+        cp_async_wait<0>();
+        grp_sync<T>(warp);
+        constexpr bool V4 = NP == 4 && sizeof(Real) == 4 && VS;   // a face-trace row is one float4
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+            for (int it = 0; it < NFI; ++it) {
+                const int t = lane + T * it;
+                if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
+                const int side = t >= NFP ? 1 : 0;
+                const int fp = t - side * NFP;
+                const int f = 2 * d + side;
+                const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
+                const Real* N = Nr[d][it];
+                // jumps
+                Real uL[NV], jv[NV];
+                const Real* tf = sl + f * NV * NFP;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) uL[v] = tf[v * NFP + fp];
+                if (!BND || code >= 0) {
+                    const Real* un = sn + f * NV * NFP;
+                    const int fpn = omap<DIM, NP>(code & 7, fp);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) jv[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]) - uL[v];
+                } else {
+                    Real ug[NV], uc[NV];
+                    bc_state<DIM>(-code, uL, N, ph, ug, uc);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) jv[v] = uc[v] - uL[v];
+                }
+                // reference derivatives at the face point: across the face
+                // (normal line of the volume) and along its two directions
+                // (rows of D applied to the face trace)
+                const int a = fp % NP, b = DIM == 3 ? fp / NP : 0;
+                Real q[DIM][NV];
+                if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+                    for (int v = 0; v + 1 < NV; v += 2) {
+                        Real l0[NP], l1[NP];
+                        vload_line<DIM, P>(su, v, d, fp, l0);
+                        vload_line<DIM, P>(su, v + 1, d, fp, l1);
+                        float2 qn = make_float2(0.0f, 0.0f), qa = qn, qb = qn;
+                        Real r0[NP], r1[NP];
+                        if constexpr (V4) {
+                            const float4 x0 = *reinterpret_cast<const float4*>(tf + v * NFP + NP * b);
+                            const float4 x1 = *reinterpret_cast<const float4*>(tf + (v + 1) * NFP + NP * b);
+                            r0[0] = x0.x; r0[1] = x0.y; r0[2] = x0.z; r0[3] = x0.w;
+                            r1[0] = x1.x; r1[1] = x1.y; r1[2] = x1.z; r1[3] = x1.w;
+                        } else {
+#pragma unroll
+                            for (int k2 = 0; k2 < NP; ++k2) {
+                                r0[k2] = tf[v * NFP + NP * b + k2];
+                                r1[k2] = tf[(v + 1) * NFP + NP * b + k2];
+                            }
+                        }
+#pragma unroll
+                        for (int k2 = 0; k2 < NP; ++k2) {
+                            const Real dn = side ? -op.dlm[NP - 1 - k2] : op.dlm[k2];
+                            qn = __ffma2_rn(make_float2(dn, dn), make_float2(l0[k2], l1[k2]), qn);
+                            const Real da = op.D[a * MAXNP + k2];
+                            qa = __ffma2_rn(make_float2(da, da), make_float2(r0[k2], r1[k2]), qa);
+                            if constexpr (DIM == 3) {
+                                const Real db = op.D[b * MAXNP + k2];
+                                qb = __ffma2_rn(make_float2(db, db),
+                                                make_float2(tf[v * NFP + a + k2 * NP], tf[(v + 1) * NFP + a + k2 * NP]),
+                                                qb);
+                            }
+                        }
+                        q[d][v] = qn.x;
+                        q[d][v + 1] = qn.y;
+                        q[d == 0 ? 1 : 0][v] = qa.x;
+                        q[d == 0 ? 1 : 0][v + 1] = qa.y;
+                        if constexpr (DIM == 3) {
+                            q[d == 2 ? 1 : 2][v] = qb.x;
+                            q[d == 2 ? 1 : 2][v + 1] = qb.y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = sizeof(Real) == 4 ? NV - NV % 2 : 0; v < NV; ++v) {
+                    Real ln[NP];
+                    vload_line<DIM, P>(su, v, d, fp, ln);
+                    Real qn = Real(0), qa = Real(0), qb = Real(0);
+#pragma unroll
+                    for (int k2 = 0; k2 < NP; ++k2) {
+                        const Real dn = side ? -op.dlm[NP - 1 - k2] : op.dlm[k2];
+                        qn += dn * ln[k2];
+                        qa += op.D[a * MAXNP + k2] * tf[v * NFP + NP * b + k2];
+                        if constexpr (DIM == 3) qb += op.D[b * MAXNP + k2] * tf[v * NFP + a + k2 * NP];
+                    }
+                    q[d][v] = qn;
+                    q[d == 0 ? 1 : 0][v] = qa;
+                    if constexpr (DIM == 3) q[d == 2 ? 1 : 2][v] = qb;
+                }
+                // lifted physical gradient G = (1/|J|) S^T q + eta lc (u_c - u_f),
+                // lc = nsign l(-1).h_-(x) S[d][:] / |J| (the single-face lifting)
+                const Real nsg = side ? Real(1) : Real(-1);
+                Real G[NV][DIM];
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) {
+                    const Real lci = ph.eta * nsg * op.lhm * S[d * DIM + i] * iJ;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        Real tr;
+                        if constexpr (diag) {
+                            tr = S[i * DIM + i] * q[i][v] * iJ;
+                        } else {
+                            Real acc = Real(0);
+#pragma unroll
+                            for (int dd = 0; dd < DIM; ++dd) acc += S[dd * DIM + i] * q[dd][v];
+                            tr = acc * iJ;
+                        }
+                        G[v][i] = tr + lci * jv[v];
+                    }
+                }
+                Real Fn[NV];
+                if (!BND || code >= 0) {
+                    visc_flux_n<DIM>(uL, G, ph.mu, ph.kappa, N, Fn);
+                } else {
+                    Real ug[NV], ub[NV];
+                    bc_state<DIM>(-code, uL, N, ph, ug, ub);
+                    visc_flux_n<DIM>(ub, G, ph.mu, ph.kappa, N, Fn);
+                    if (code == -FR_BC_WALL) Fn[NV - 1] = Real(0);
+                }
+                Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dst[v * NFP] = Fn[v];
+            }
+        }
+    } else {
     // B: jumps per face point
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -851,7 +1056,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
         }
     }
     grp_sync<T>(warp);  // the gradient below overwrites the staged neighbour traces
-    if constexpr (curved) {
+    {
         // C1: uncorrected reference gradient along lines: q_d = D_d u
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -909,8 +1114,6 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                     sg[VL::pt(i * NV + v, sp)] = acc * iJ;
                 }
         }
-    } else {
-        cp_async_wait<0>();
     }
     // normals of this lane's face points, all directions at once
     Real Nr[DIM][NFI][DIM];
@@ -922,29 +1125,6 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             const int side = t >= NFP ? 1 : 0;
             if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
         }
-    // affine: per face point of this lane, the derivative coefficients along
-    // the face (rows of D for its two in-face coordinates a, b, and where the
-    // face point's line along a / b starts in the face trace) and across it
-    // (l_j'(-1), or l_j'(+1) = -l_{NP-1-j}'(-1))
-    Real Da[NFI][NP], Db[NFI][NP], dn[NFI][NP];
-    int fa[NFI], fb[NFI];
-    if constexpr (!curved) {
-#pragma unroll
-        for (int it = 0; it < NFI; ++it) {
-            const int t = min(lane + T * it, 2 * NFP - 1);
-            const int side = t >= NFP ? 1 : 0;
-            const int fp = t - side * NFP;
-            const int a = fp % NP, b = DIM == 3 ? fp / NP : 0;
-            fa[it] = NP * b;     // line along a: points k + NP b
-            fb[it] = a;          // line along b: points a + NP k
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                Da[it][k] = op.D[a * MAXNP + k];
-                Db[it][k] = op.D[b * MAXNP + k];
-                dn[it][k] = side ? -op.dlm[NP - 1 - k] : op.dlm[k];
-            }
-        }
-    }
     grp_sync<T>(warp);
     // D: lifted face gradient, viscous normal flux
 #pragma unroll
@@ -961,11 +1141,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
             face_coefs<DIM, P>(op, side, cf);
             // lifting coefficient along the line: nsign sum_j l_j h_j S_j[d][i] / J_j
             Real lc[DIM];
-            if (!curved) {
-                const Real iJ = g.iJ[e * g.sJ_e];
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) lc[i] = nsg * op.lhm * g.S[e * g.sS_e + (d * DIM + i) * g.sS_k] * iJ;
-            } else {
+            {
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) lc[i] = Real(0);
 #pragma unroll
@@ -981,53 +1157,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 for (int i = 0; i < DIM; ++i) lc[i] *= nsg;
             }
             Real tr[DIM * NV];   // traces of the physical gradient [i][v]
-            if constexpr (curved) {
-                traces_at<DIM, P, DIM * NV>(sg, d, fp, cf, tr);
-            } else {
-                // affine: the metrics are constant, so the trace of (1/|J|) S^T D u
-                // is (1/|J|) S^T applied to the traces of the reference
-                // derivatives.  Along the face those are the derivatives of the
-                // face trace (interpolation to the face and differentiation along
-                // it commute); across it, the derivative of the normal line at
-                // its end, sum_j l_j'(+-1) u_j.
-                Real q[DIM][NV];
-                const Real* tf = sl + f * NV * NFP;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    Real ln[NP];
-                    vload_line<DIM, P>(su, v, d, fp, ln);
-                    Real acc = Real(0);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) acc += dn[it][j] * ln[j];
-                    q[d][v] = acc;
-                    Real qa = Real(0);
-#pragma unroll
-                    for (int k = 0; k < NP; ++k) qa += Da[it][k] * tf[v * NFP + fa[it] + k];
-                    q[d == 0 ? 1 : 0][v] = qa;
-                    if constexpr (DIM == 3) {
-                        Real qb = Real(0);
-#pragma unroll
-                        for (int k = 0; k < NP; ++k) qb += Db[it][k] * tf[v * NFP + fb[it] + k * NP];
-                        q[d == 2 ? 1 : 2][v] = qb;
-                    }
-                }
-                Real S[DIM * DIM];
-                load_S<DIM>(g, e, 0, S);
-                const Real iJ = g.iJ[e * g.sJ_e];
-#pragma unroll
-                for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        if constexpr (diag) {
-                            tr[i * NV + v] = S[i * DIM + i] * q[i][v] * iJ;
-                        } else {
-                            Real acc = Real(0);
-#pragma unroll
-                            for (int dd = 0; dd < DIM; ++dd) acc += S[dd * DIM + i] * q[dd][v];
-                            tr[i * NV + v] = acc * iJ;
-                        }
-                    }
-            }
+            traces_at<DIM, P, DIM * NV>(sg, d, fp, cf, tr);
             Real G[NV][DIM];
             Real uL[NV];
 #pragma unroll
@@ -1057,6 +1187,7 @@ __global__ void k_visc_face(const Real* __restrict__ u, const Real* __restrict__
                 dst[v * NFP] = acc;
             }
         }
+    }
     }
 }
 
