@@ -373,12 +373,18 @@ struct Smem {
     static constexpr int G = DIM * DIM * Z::NSP + Z::NSP;
     static constexpr int visc_c = visc + G;
     static constexpr int resid_c = rE + imax(F, G);
+    // pipelined face kernel on affine meshes: two buffers per element group,
+    // each [state U | own traces F | neighbour traces F | S, 1/|J|, normals]
+    static constexpr int GEO = (DIM * DIM + 1 + 2 * DIM * DIM + 3) / 4 * 4;
+    static constexpr int pl = U, pn = U + F, pg = U + 2 * F;
+    static constexpr int visc_buf = (pg + GEO + 3) / 4 * 4;
+    static constexpr int visc_p = 2 * visc_buf;
 };
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_traces(int wpb) { return sizeof(Real) * size_t(wpb) * Smem<DIM, P>::traces; }
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_visc(int wpb, bool curved) {
-    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::visc_c : Smem<DIM, P>::visc_a);
+    return sizeof(Real) * size_t(wpb) * (curved ? Smem<DIM, P>::visc_c : Smem<DIM, P>::visc_p);
 }
 template <int DIM, int P, typename Real>
 __host__ __device__ constexpr size_t smem_resid(int wpb, bool curved) {
@@ -814,91 +820,30 @@ __global__ void k_traces(const Real* __restrict__ u, Real* __restrict__ uf, int6
     warp_write_traces<DIM, P, T>(su, uf + e * NF * NV * NFP, op, lane);
 }
 
-// Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
-// boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
-// an adiabatic wall) is written instead.  MP is the mesh's metric path, fixed
-// at compile time: 0 per-point metrics (curved), 1 one metric set per element
-// (affine), 2 affine with diagonal S (axis-aligned); BND false: the mesh has
-// no boundary faces (fully periodic), so the boundary-state code is left out.
-template <int DIM, int P, typename Real, int MP, bool BND>
-__global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
-                            int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
-                            const __grid_constant__ Geo<Real> g) {
+// Sweep B on affine elements: one element's face phase from its staged data
+// (state su, own traces sl, neighbour traces sn, sgeo = S[DIM*DIM], 1/|J|,
+// the outward area normals [NF][DIM]), one pass per face point: the jump
+// u_c - u_f, the lifted face gradient and the viscous normal flux, all in
+// registers.  With constant metrics the trace of (1/|J|) S^T D u is (1/|J|)
+// S^T applied to the traces of the reference derivatives: along the face the
+// derivatives of the face trace (interpolation to the face and
+// differentiation along it commute), across it the derivative of the normal
+// line at its end, sum_j l_j'(+-1) u_j.
+template <int DIM, int P, typename Real, bool diag, bool BND, bool VS>
+__device__ __forceinline__ void visc_faces_affine(const Real* su, const Real* sl, const Real* sn, const Real* sgeo,
+                                                  const int (&codes)[2 * DIM], int64_t e, Real* __restrict__ fvn,
+                                                  const Ops<Real>& op, const Phys<Real>& ph, int lane) {
     using Z = Sz<DIM, P>;
-    constexpr int T = Grp<DIM, P>::T;   // threads per element
-    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
-    constexpr int NSPW = (NSP + T - 1) / T;           // solution points per lane
-    constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
-    constexpr int NLI = (NL + T - 1) / T;             // ... per lane
-    constexpr int NFI = (2 * NFP + T - 1) / T;        // face points of one direction per lane
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x / T, lane = threadIdx.x % T;
-    const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
-    if (e >= E) return;
-    using SM = Smem<DIM, P>;
-    using VL = Vol<DIM, P, Real>;
-    constexpr bool curved = MP == 0;                // per-point metrics, staged after region D
-    constexpr bool diag = MP == 2;                  // affine, diagonal S
-    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc_a);
-    Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
-    Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
-    Real* sg = su + SM::vD;              // gradient          [d or i][v][sp]
-    Real* sn = sg;                       // staged neighbour traces [f][v][fp] (face phase only)
-    Real* sS = su + SM::visc;            // curved: S [k][sp], 1/|J| [sp]
-    // face codes of this element, broadcast to every lane
-    int codes[NF];
+    constexpr int T = Grp<DIM, P>::T;
+    constexpr int NP = Z::NP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    constexpr int NFI = (2 * NFP + T - 1) / T;
     {
-        const int mine = (lane & 31) < NF ? g.nbr[e * NF + (lane & 31)] : 0;
+        // the element's metrics and normals, staged with its data
+        const Real* S = sgeo;
+        const Real iJ = sgeo[DIM * DIM];
+        Real SJ[DIM * DIM];   // S / |J|, the element's constant dxi_d/dx_i
 #pragma unroll
-        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
-    }
-    // stage the element state, its own and its neighbours' face traces (the
-    // traces array holds them for every element) and (curved) the metrics, in
-    // three groups
-    constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0 &&
-                        (SM::visc_a * sizeof(Real)) % 16 == 0;
-    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0 &&
-                        (SM::vC * sizeof(Real)) % 16 == 0;
-    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane, T);
-    cp_async_commit();
-    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane, T);
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-        if (!BND || codes[f] >= 0)
-            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
-    cp_async_commit();
-    if (curved) {
-        warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane, T);
-        warp_stage_auto<NSP, VW && ((SM::visc + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
-            sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane, T);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();
-    grp_sync<T>(warp);
-    if constexpr (!curved) {
-        // Affine elements, one pass per face point: the jump u_c - u_f, the
-        // lifted face gradient and the viscous normal flux, all in registers.
-        // With constant metrics the trace of (1/|J|) S^T D u is (1/|J|) S^T
-        // applied to the traces of the reference derivatives: along the face
-        // the derivatives of the face trace (interpolation to the face and
-        // differentiation along it commute), across it the derivative of the
-        // normal line at its end, sum_j l_j'(+-1) u_j.
-        // the normals of this lane's face points and the element's metrics:
-        // loads issued before the wait for the staged arrays
-        Real Nr[DIM][NFI][DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-#pragma unroll
-            for (int it = 0; it < NFI; ++it) {
-                const int t = lane + T * it;
-                const int side = t >= NFP ? 1 : 0;
-                if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
-            }
-        Real S[DIM * DIM];
-        load_S<DIM>(g, e, 0, S);
-        const Real iJ = g.iJ[e * g.sJ_e];
-        cp_async_wait<0>();
-        grp_sync<T>(warp);
+        for (int k2 = 0; k2 < DIM * DIM; ++k2) SJ[k2] = S[k2] * iJ;
         constexpr bool V4 = NP == 4 && sizeof(Real) == 4 && VS;   // a face-trace row is one float4
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -910,7 +855,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
                 const int fp = t - side * NFP;
                 const int f = 2 * d + side;
                 const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
-                const Real* N = Nr[d][it];
+                const Real* N = sgeo + DIM * DIM + 1 + f * DIM;
                 // jumps
                 Real uL[NV], jv[NV];
                 const Real* tf = sl + f * NV * NFP;
@@ -920,7 +865,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
                     const Real* un = sn + f * NV * NFP;
                     const int fpn = omap<DIM, NP>(code & 7, fp);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) jv[v] = Real(0.5) * (uL[v] + un[v * NFP + fpn]) - uL[v];
+                    for (int v = 0; v < NV; ++v) jv[v] = Real(0.5) * (un[v * NFP + fpn] - uL[v]);
                 } else {
                     Real ug[NV], uc[NV];
                     bc_state<DIM>(-code, uL, N, ph, ug, uc);
@@ -997,17 +942,16 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
                 Real G[NV][DIM];
 #pragma unroll
                 for (int i = 0; i < DIM; ++i) {
-                    const Real lci = ph.eta * nsg * op.lhm * S[d * DIM + i] * iJ;
+                    const Real lci = ph.eta * nsg * op.lhm * SJ[d * DIM + i];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         Real tr;
                         if constexpr (diag) {
-                            tr = S[i * DIM + i] * q[i][v] * iJ;
+                            tr = SJ[i * DIM + i] * q[i][v];
                         } else {
-                            Real acc = Real(0);
+                            tr = Real(0);
 #pragma unroll
-                            for (int dd = 0; dd < DIM; ++dd) acc += S[dd * DIM + i] * q[dd][v];
-                            tr = acc * iJ;
+                            for (int dd = 0; dd < DIM; ++dd) tr += SJ[dd * DIM + i] * q[dd][v];
                         }
                         G[v][i] = tr + lci * jv[v];
                     }
@@ -1026,7 +970,142 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
                 for (int v = 0; v < NV; ++v) dst[v * NFP] = Fn[v];
             }
         }
-    } else {
+    }
+}
+
+// Sweep B on affine meshes, pipelined: a persistent grid of element groups,
+// each walking the elements e0, e0 + G, e0 + 2G, ... (G groups in the grid).
+// While a group computes one element's face phase from one shared buffer, the
+// cp.async copies of its next element (state, own and neighbour traces,
+// metrics, normals) fill the other buffer, so the copy latency overlaps the
+// arithmetic; the neighbour codes are read two elements ahead.
+template <int DIM, int P, typename Real, int MP, bool BND>
+__global__ void k_visc_face_aff(
+    const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn, int64_t E,
+    const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph, const __grid_constant__ Geo<Real> g) {
+    using Z = Sz<DIM, P>;
+    constexpr int T = Grp<DIM, P>::T;   // threads per element
+    constexpr int NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    using SM = Smem<DIM, P>;
+    constexpr int BUF = SM::visc_buf;
+    constexpr int NGEO = DIM * DIM + 1 + NF * DIM;
+    static_assert(MP != 0, "affine meshes only");
+    constexpr bool VS = (BUF * sizeof(Real)) % 16 == 0 && (NV * NFP * sizeof(Real)) % 16 == 0 &&
+                        (SM::pl * sizeof(Real)) % 16 == 0 && (SM::pn * sizeof(Real)) % 16 == 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int grp = threadIdx.x / T, lane = threadIdx.x % T, lw = lane & 31;
+    const int64_t G = int64_t(gridDim.x) * (blockDim.x / T);
+    int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + grp;
+    if (e >= E) return;
+    Real* const buf = reinterpret_cast<Real*>(smem) + grp * 2 * BUF;
+    auto stage = [&](int64_t el, Real* b, int mine) {
+        int codes[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
+        warp_stage_vol<DIM, P>(b, u + el * NV * NSP, lane, T);
+        warp_stage<NF * NV * NFP, VS>(b + SM::pl, uf + el * NF * NV * NFP, lane, T);
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+            if (!BND || codes[f] >= 0)
+                warp_stage<NV * NFP, VS>(b + SM::pn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
+        for (int k = lane; k < NGEO; k += T) {
+            const Real* src = k < DIM * DIM ? g.S + el * g.sS_e + k * g.sS_k
+                            : k == DIM * DIM ? g.iJ + el * g.sJ_e
+                                             : g.N + (el * NF) * g.sN_f + (k - DIM * DIM - 1);
+            cp_async_small<int(sizeof(Real))>(b + SM::pg + k, src);
+        }
+    };
+    int mineA = lw < NF ? g.nbr[e * NF + lw] : 0;                 // codes of e
+    int64_t en = e + G;
+    int mineB = (en < E && lw < NF) ? g.nbr[en * NF + lw] : 0;   // codes of the next element
+    stage(e, buf, mineA);
+    cp_async_commit();
+    int b = 0;
+    for (;;) {
+        Real* cur = buf + b * BUF;
+        if (en < E) stage(en, buf + (b ^ 1) * BUF, mineB);
+        cp_async_commit();
+        const int64_t enn = en + G;
+        const int mineC = (enn < E && lw < NF) ? g.nbr[enn * NF + lw] : 0;
+        cp_async_wait<1>();
+        grp_sync<T>(grp);
+        int codes[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mineA, f);
+        visc_faces_affine<DIM, P, Real, MP == 2, BND, VS>(cur, cur + SM::pl, cur + SM::pn, cur + SM::pg, codes, e,
+                                                          fvn, op, ph, lane);
+        if (en >= E) break;
+        grp_sync<T>(grp);   // every thread is done with cur before it is refilled
+        e = en;
+        en = enn;
+        mineA = mineB;
+        mineB = mineC;
+        b ^= 1;
+    }
+}
+
+// Sweep B: BR2 face gradients and the own-side viscous normal flux.  For a
+// boundary face the common viscous flux F_vis(u_b, G).N (energy entry zero at
+// an adiabatic wall) is written instead.  MP is the mesh's metric path, fixed
+// at compile time: 0 per-point metrics (curved), 1 one metric set per element
+// (affine), 2 affine with diagonal S (axis-aligned); BND false: the mesh has
+// no boundary faces (fully periodic), so the boundary-state code is left out.
+template <int DIM, int P, typename Real, int MP, bool BND>
+__global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real* __restrict__ u, const Real* __restrict__ uf, Real* __restrict__ fvn,
+                            int64_t E, const __grid_constant__ Ops<Real> op, const __grid_constant__ Phys<Real> ph,
+                            const __grid_constant__ Geo<Real> g) {
+    using Z = Sz<DIM, P>;
+    constexpr int T = Grp<DIM, P>::T;   // threads per element
+    constexpr int NP = Z::NP, NSP = Z::NSP, NFP = Z::NFP, NF = Z::NF, NV = Z::NV;
+    constexpr int NSPW = (NSP + T - 1) / T;           // solution points per lane
+    constexpr int NL = NV * NFP;                    // (variable, line) tasks per direction
+    constexpr int NLI = (NL + T - 1) / T;             // ... per lane
+    constexpr int NFI = (2 * NFP + T - 1) / T;        // face points of one direction per lane
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x / T, lane = threadIdx.x % T;
+    const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
+    if (e >= E) return;
+    using SM = Smem<DIM, P>;
+    using VL = Vol<DIM, P, Real>;
+    constexpr bool curved = MP == 0;                // per-point metrics, staged after region D
+    constexpr bool diag = MP == 2;                  // affine, diagonal S
+    Real* su = reinterpret_cast<Real*>(smem) + warp * (curved ? SM::visc_c : SM::visc_a);
+    Real* sj = su + SM::vB;              // jumps u_c - u_f   [f][v][fp]
+    Real* sl = su + SM::vC;              // own traces u_f    [f][v][fp]
+    Real* sg = su + SM::vD;              // gradient          [d or i][v][sp]
+    Real* sn = sg;                       // staged neighbour traces [f][v][fp] (face phase only)
+    Real* sS = su + SM::visc;            // curved: S [k][sp], 1/|J| [sp]
+    // face codes of this element, broadcast to every lane
+    int codes[NF];
+    {
+        const int mine = (lane & 31) < NF ? g.nbr[e * NF + (lane & 31)] : 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
+    }
+    // stage the element state, its own and its neighbours' face traces (the
+    // traces array holds them for every element) and (curved) the metrics, in
+    // three groups
+    constexpr bool VW = (SM::visc * sizeof(Real)) % 16 == 0 && (SM::visc_c * sizeof(Real)) % 16 == 0 &&
+                        (SM::visc_a * sizeof(Real)) % 16 == 0;
+    constexpr bool VS = VW && (NV * NFP * sizeof(Real)) % 16 == 0 && (SM::vD * sizeof(Real)) % 16 == 0 &&
+                        (SM::vC * sizeof(Real)) % 16 == 0;
+    warp_stage_vol<DIM, P>(su, u + e * NV * NSP, lane, T);
+    cp_async_commit();
+    warp_stage<NF * NV * NFP, VS>(sl, uf + e * NF * NV * NFP, lane, T);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+        if (!BND || codes[f] >= 0)
+            warp_stage<NV * NFP, VS>(sn + f * NV * NFP, uf + int64_t(codes[f] >> 3) * NV * NFP, lane, T);
+    cp_async_commit();
+    if (curved) {
+        warp_stage_auto<DIM * DIM * NSP, VW>(sS, g.S + e * g.sS_e, lane, T);
+        warp_stage_auto<NSP, VW && ((SM::visc + DIM * DIM * NSP) * sizeof(Real)) % 16 == 0>(
+            sS + DIM * DIM * NSP, g.iJ + e * g.sJ_e, lane, T);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    grp_sync<T>(warp);
+    {
     // B: jumps per face point
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {

@@ -2,6 +2,8 @@
 // including translation unit defines FR_REAL and FR_DIM.
 #include "fr_kernels.cuh"
 
+#include <algorithm>
+
 namespace frl {
 
 namespace {
@@ -38,17 +40,53 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& 
 // metric path of the kernels: 0 per-point metrics, 1 affine, 2 affine with diagonal S
 inline int metric_path(const frk::Geo<FR_REAL>& g) { return g.sS_sp != 0 ? 0 : g.diag ? 2 : 1; }
 
+// Blocks of a persistent launch: as many as fit on every SM at once (threads,
+// registers in units of 8 per thread, shared memory with 1 KB reserved per
+// block), at most one per tile of elements.
+inline unsigned persistent_grid(int64_t E, int epb, int threads, size_t smem, int regs, int nsm) {
+    const int r8 = (std::max(regs, 1) + 7) / 8 * 8;
+    int per = std::min(2048 / threads, 32);
+    per = std::min(per, 65536 / (threads * r8));
+    per = std::min(per, int(233472 / (smem + 1024)));
+    const int64_t cap = int64_t(std::max(per, 1)) * std::max(nsm, 1);
+    return unsigned(std::min<int64_t>(int64_t(grid_of(E, epb)), cap));
+}
+
 template <int P, int MP, bool BND>
 int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const frk::Ops<FR_REAL>& op,
            const frk::Phys<FR_REAL>& ph, const frk::Geo<FR_REAL>& g, frk::Launch lc, cudaStream_t s) {
-    auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP, BND>;
-    const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
-    static bool done = false;
-    cudaError_t e = prep(k, sm, done);
-    if (e != cudaSuccess) return int(e);
-    if (E == 0) return 0;
-    k<<<grid_of(E, lc.epb), frk::Grp<FR_DIM, P>::T * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g);
-    return int(cudaGetLastError());
+    if constexpr (MP == 0) {
+        auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP, BND>;
+        const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, true);
+        static bool done = false;
+        cudaError_t e = prep(k, sm, done);
+        if (e != cudaSuccess) return int(e);
+        if (E == 0) return 0;
+        k<<<grid_of(E, lc.epb), frk::Grp<FR_DIM, P>::T * lc.epb, sm, s>>>(u, uf, fvn, E, op, ph, g);
+        return int(cudaGetLastError());
+    } else {
+        // affine meshes: the pipelined kernel on a persistent grid, sized from
+        // the kernel's registers and the SM count read at set-up (the first,
+        // empty launch at mesh load, outside any stream capture)
+        auto k = frk::k_visc_face_aff<FR_DIM, P, FR_REAL, MP, BND>;
+        const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, false);
+        static bool done = false;
+        static int regs = 0, nsm = 0;
+        cudaError_t e = prep(k, sm, done);
+        if (e != cudaSuccess) return int(e);
+        if (!regs) {
+            cudaFuncAttributes fa;
+            int dev = 0;
+            if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return int(e);
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return int(e);
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return int(e);
+            regs = fa.numRegs;
+        }
+        if (E == 0) return 0;
+        const int threads = frk::Grp<FR_DIM, P>::T * lc.epb;
+        k<<<persistent_grid(E, lc.epb, threads, sm, regs, nsm), threads, sm, s>>>(u, uf, fvn, E, op, ph, g);
+        return int(cudaGetLastError());
+    }
 }
 
 template <int P, int MP, bool VISC, bool BND>
