@@ -81,8 +81,11 @@ __device__ __forceinline__ void sp_split(int sp, int d, int& fp, int& j) {
 }
 
 // neighbour face point matching face point fp for orientation code o
+// (o = 0, the identity, is the common case: the code is uniform over the
+// face, so the branch costs no divergence)
 template <int DIM, int NP>
 __device__ __forceinline__ int omap(int o, int fp) {
+    if (o == 0) return fp;
     if (DIM == 2) return (o & 1) ? NP - 1 - fp : fp;
     int a = fp % NP, b = fp / NP;
     if (o & 4) { const int t = a; a = b; b = t; }

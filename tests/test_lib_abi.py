@@ -111,6 +111,26 @@ def test_new_entry_points_reject_bad_input_on_host(lib):
     assert lib.fr_set_adaptive_dt(None, 0.5) == F.FR_EINVAL
     assert lib.fr_cand_dt(None, 0, C.byref(t)) == F.FR_EINVAL
     assert lib.fr_set_element_order(None, -1, None) == F.FR_EINVAL
+    flag = C.c_int()
+    assert lib.fr_nonfinite(None, -1, C.byref(flag)) == F.FR_EINVAL
+    assert lib.fr_set_rk_scheme(None, 0, None) == F.FR_EINVAL
+
+
+def test_tensor_core_modes_are_validated_on_host(lib):
+    # the tensor-core precision modes exist in 3D at p = 3 and 4 only; other
+    # requests fail before any device work
+    from paper_2501_05709_gb300 import workloads as W
+    out = C.c_void_p()
+    nodes, conn = W.box_mesh(2, 2, 0.0, 1.0)
+    d = _desc(nodes, conn.astype(np.int32))
+    assert lib.fr_mesh_load(C.byref(d), 1, C.byref(F.options(order=3, precision=F.FR_TF32_TC)),
+                            C.byref(out)) == F.FR_EINVAL
+    nodes, conn = W.box_mesh(3, 2, 0.0, 1.0)
+    d = _desc(nodes, conn.astype(np.int32))
+    assert lib.fr_mesh_load(C.byref(d), 1, C.byref(F.options(order=2, precision=F.FR_BF16X3_TC)),
+                            C.byref(out)) == F.FR_EINVAL
+    assert b"tensor-core" in lib.fr_last_error()
+    assert lib.fr_mesh_load(C.byref(d), 1, C.byref(F.options(order=3, precision=7)), C.byref(out)) == F.FR_EINVAL
 
 
 def _function_body(src, name):
