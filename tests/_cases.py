@@ -29,6 +29,19 @@ def make_case(name):
         c["nodes"], c["conn"] = W.box_mesh(3, [5, 5, 3], 0.0, 2 * math.pi, q=1)
         c.update(p=3, mu=1.0 / 1600.0, visc=True, dt=2.5e-4)
         c["state"] = lambda x: _conserved_at(x, W.taylor_green, mach=0.1)
+    elif name == "tgv3d_p4":
+        # affine box at p = 4: two warps per element, the pipelined face kernel
+        c["nodes"], c["conn"] = W.box_mesh(3, [4, 3, 3], 0.0, 2 * math.pi, q=1)
+        c.update(p=4, mu=1.0 / 1600.0, visc=True, dt=1.5e-4)
+        c["state"] = lambda x: _conserved_at(x, W.taylor_green, mach=0.1)
+    elif name == "rot3d_p4":
+        ax = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = np.eye(3) + math.sin(0.5) * K + (1 - math.cos(0.5)) * K @ K
+        nodes, c["conn"] = W.box_mesh(3, [3, 3, 2], 0.0, 1.0, q=1)
+        c["nodes"] = np.ascontiguousarray(np.asarray(nodes) @ R.T)
+        c.update(p=4, mu=0.02, visc=True)
+        c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=15)
     elif name == "ns3d_curved_p3":
         c["nodes"], c["conn"] = W.box_mesh(3, 3, 0.0, 1.0, q=2, curve=0.1, seed=3)
         c.update(p=3, mu=0.02, visc=True)
@@ -132,7 +145,7 @@ def make_case(name):
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
          "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2", "turned3d_curved_p3", "turned3d_affine_p3",
-         "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2"]
+         "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2", "tgv3d_p4", "rot3d_p4"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):
