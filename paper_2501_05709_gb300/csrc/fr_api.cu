@@ -826,11 +826,25 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
                 for (int i = 0; i < dim; ++i)
                     if (i != d && std::fabs(row[i]) > 1e-13 * mx) diag = false;
             }
+        for (int64_t e = 0; e < E && diag; ++e)
+            for (int f = 0; f < nf && diag; ++f) {
+                const double* nv = &N1[(e * nf + f) * dim];
+                double mx = 0.0;
+                for (int i = 0; i < dim; ++i) mx = std::max(mx, std::fabs(nv[i]));
+                for (int i = 0; i < dim; ++i)
+                    if (i != f / 2 && std::fabs(nv[i]) > 1e-13 * mx) diag = false;
+            }
+        // (and so do the matching components of the face normals: the normal of
+        // a face of direction d lies along axis d, which the kernels assume)
         if (diag)
-            for (int64_t e = 0; e < E; ++e)
+            for (int64_t e = 0; e < E; ++e) {
                 for (int d = 0; d < dim; ++d)
                     for (int i = 0; i < dim; ++i)
                         if (i != d) S1[e * dim * dim + d * dim + i] = 0.0;
+                for (int f = 0; f < nf; ++f)
+                    for (int i = 0; i < dim; ++i)
+                        if (i != f / 2) N1[(e * nf + f) * dim + i] = 0.0;
+            }
         c->diag = diag ? 1 : 0;
         // the larger (element, face) side takes the exact negative of the
         // smaller side's constant normal, so common fluxes stay equal and opposite

@@ -237,6 +237,78 @@ __device__ __forceinline__ void visc_flux_n(const Real* u, const Real (*G)[DIM],
     Fn[NV - 1] = en + kappa * gn;
 }
 
+// visc_flux_n for an area normal along axis d (N = Nd e_d, axis-aligned
+// elements): only column d of the flux tensor is formed, the terms that the
+// zero components of N would cancel are left out, and the surviving ones keep
+// visc_flux_n's order of operations.
+template <int DIM, typename Real>
+__device__ __forceinline__ void visc_flux_axis(const Real* u, const Real (*G)[DIM], Real mu, Real kappa, int d,
+                                               Real Nd, Real* Fn) {
+    constexpr int NV = DIM + 2;
+    const Real ir = Real(1) / u[0];
+    Real V[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) V[i] = u[1 + i] * ir;
+    Real gV[DIM][DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) gV[i][j] = (G[1 + i][j] - V[i] * G[0][j]) * ir;
+    const Real Er = u[NV - 1] * ir;
+    Real s = (G[NV - 1][d] - Er * G[0][d]) * ir;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) s -= V[i] * gV[i][d];
+    const Real gn = s * Nd;
+    Real div = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) div += gV[i][i];
+    const Real c23 = Real(2.0 / 3.0) * mu * div;
+    Real en = Real(0);
+    Fn[0] = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        const Real a = (gV[i][d] + gV[d][i]) * Nd;
+        const Real tn = i == d ? mu * a - c23 * Nd : mu * a;
+        Fn[1 + i] = tn;
+        en += V[i] * tn;
+    }
+    Fn[NV - 1] = en + kappa * gn;
+}
+
+// Rusanov flux for an area normal along axis d (N = Nd e_d): rusanov with the
+// zero components of N left out.
+template <int DIM, typename Real>
+__device__ __forceinline__ void rusanov_axis(const Real* uL, const Real* uR, int d, Real Nd, Real gamma, Real gm1,
+                                             Real* F) {
+    constexpr int NV = DIM + 2;
+    const Real a2 = Nd * Nd;
+    const Real ia = rsqrt(a2);
+    const Real area = a2 * ia;
+    const Real nd = Nd * ia;
+    const Real irL = Real(1) / uL[0], irR = Real(1) / uR[0];
+    Real m2L = Real(0), m2R = Real(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        m2L += uL[1 + i] * uL[1 + i];
+        m2R += uR[1 + i] * uR[1 + i];
+    }
+    const Real mnL = uL[1 + d] * nd, mnR = uR[1 + d] * nd;
+    const Real pL = gm1 * (uL[NV - 1] - Real(0.5) * m2L * irL);
+    const Real pR = gm1 * (uR[NV - 1] - Real(0.5) * m2R * irR);
+    const Real vL = mnL * irL, vR = mnR * irR;
+    const Real cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+    const Real lam = fmax(fabs(vL) + cL, fabs(vR) + cR);
+    const Real h = Real(0.5) * area;
+    const Real hl = h * lam;
+    F[0] = h * (mnL + mnR) - hl * (uR[0] - uL[0]);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        const Real fl = i == d ? uL[1 + i] * vL + uR[1 + i] * vR + (pL + pR) * nd : uL[1 + i] * vL + uR[1 + i] * vR;
+        F[1 + i] = h * fl - hl * (uR[1 + i] - uL[1 + i]);
+    }
+    F[NV - 1] = h * ((uL[NV - 1] + pL) * vL + (uR[NV - 1] + pR) * vR) - hl * (uR[NV - 1] - uL[NV - 1]);
+}
+
 // Boundary states: ghost for the inviscid flux and common solution u_b.
 template <int DIM, typename Real>
 __device__ __forceinline__ void bc_state(int tag, const Real* uL, const Real* N, const Phys<Real>& ph,
@@ -956,16 +1028,19 @@ __device__ __forceinline__ void visc_faces_affine(const Real* su, const Real* sl
 #pragma unroll
                             for (int dd = 0; dd < DIM; ++dd) tr += SJ[dd * DIM + i] * q[dd][v];
                         }
-                        G[v][i] = tr + lci * jv[v];
+                        // axis-aligned: S[d][i] = 0 for i != d, so is the lifting there
+                        G[v][i] = diag && i != d ? tr : tr + lci * jv[v];
                     }
                 }
                 Real Fn[NV];
                 if (!BND || code >= 0) {
-                    visc_flux_n<DIM>(uL, G, ph.mu, ph.kappa, N, Fn);
+                    if constexpr (diag) visc_flux_axis<DIM>(uL, G, ph.mu, ph.kappa, d, N[d], Fn);
+                    else visc_flux_n<DIM>(uL, G, ph.mu, ph.kappa, N, Fn);
                 } else {
                     Real ug[NV], ub[NV];
                     bc_state<DIM>(-code, uL, N, ph, ug, ub);
-                    visc_flux_n<DIM>(ub, G, ph.mu, ph.kappa, N, Fn);
+                    if constexpr (diag) visc_flux_axis<DIM>(ub, G, ph.mu, ph.kappa, d, N[d], Fn);
+                    else visc_flux_n<DIM>(ub, G, ph.mu, ph.kappa, N, Fn);
                     if (code == -FR_BC_WALL) Fn[NV - 1] = Real(0);
                 }
                 Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
@@ -1388,7 +1463,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
                 bc_state<DIM>(-code, uL, N, ph, uR, uc);
             }
             Real Fc[NV];
-            rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
+            if constexpr (diag) rusanov_axis<DIM>(uL, uR, d, N[d], ph.gamma, ph.gm1, Fc);
+            else rusanov<DIM>(uL, uR, N, ph.gamma, ph.gm1, Fc);
             if constexpr (VISC) {
                 const Real* own = so + f * NV * NFP + fp;
                 if (!BND || code >= 0) {

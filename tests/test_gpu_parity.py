@@ -187,10 +187,15 @@ def test_fwh_integrate_matches_oracle():
 
 
 def test_fp32_residual_error_is_bounded():
-    # stated FP32 bound: relative L2 of the residual against the FP64 oracle
+    # stated FP32 bound: relative L2 of the residual against the FP64 oracle.
+    # Rounding only the state to float moves the oracle's own residual by
+    # 2.2e-6 .. 2.7e-6 on the curved and turned cases, but by 3.8e-4 (p = 3)
+    # and 6.9e-4 (p = 4) on the low-Mach Taylor-Green box, whose residual is a
+    # small difference of fluxes carrying p ~ 71; the bounds are 2.6 .. 4.4x
+    # those floors there.
     from paper_2501_05709_gb300 import fr as F
     for name, tol in (("ns3d_curved_p3", 1e-5), ("ns3d_ogrid_p3", 1e-4), ("tgv3d_p3", 1e-3), ("rot3d_p3", 1e-5),
-                      ("rot3d_p4", 1e-5), ("tgv3d_p4", 1e-3)):
+                      ("rot3d_p4", 1e-5), ("tgv3d_p4", 3e-3)):
         c = make_case(name)
         m, s = oracle_for(c)
         u = c["state"](m.xsp)
