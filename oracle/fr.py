@@ -31,6 +31,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import mixed
+from .mixed import MortarOps
 from .physics import BC_FARFIELD, BC_WALL
 
 
@@ -56,7 +58,9 @@ def _expand(fv, h, d, dim, Np):
 class FRSolver:
     """Residual, RK4 and forces on one mesh for one physics.
 
-    ``caps``: optional per-element polynomial order caps (``oracle.sponge``).
+    ``caps``: optional per-element polynomial degrees q <= p; an element of
+    degree q < p is a degree-q FR element whose faces keep the degree-p flux
+    points (``oracle.mixed``).
     ``source``: optional list of Gaussian monopoles (A, k, (xs, ys, zs), freq)
     added to the energy equation (Appendix D, Eq. D.1):
     s(x, t) = sum_m A_m exp(-k_m |x - x_m|^2) sin(2 pi freq_m t), evaluated at
@@ -66,8 +70,17 @@ class FRSolver:
         self.m = mesh
         self.ph = phys
         self.source = list(source) if source else []
-        # per-element order caps (``oracle.sponge``): R <- Pi_q R on elements with q < p
+        # per-element degrees: the elements of each reduced degree q < p and
+        # their degree-q operators
         self.caps = None if caps is None else np.asarray(caps, np.int64)
+        self.reduced = []
+        if self.caps is not None:
+            for q in range(mesh.p):
+                sel = np.nonzero(self.caps == q)[0]
+                if sel.size:
+                    self.reduced.append((sel, MortarOps(mesh.p, q, mesh.ref.kind)))
+        if self.source and self.reduced:
+            raise ValueError("the energy source is defined on elements of the full degree only")
 
     def source_term(self, t):
         """s(x_sp, t) [E, Nsp] of Eq. D.1 (zeros without sources)."""
@@ -151,10 +164,13 @@ class FRSolver:
                     line = _expand(jmp[:, f], h, d, dim, Np).reshape(E, nv, -1)  # [E, nv, Nsp]
                     lift = nsg * (S[:, d] / J[:, None])[:, None] * line[:, :, None]  # [E,nv,i,Nsp]
                     Li = _contract(lift.reshape((E, nv, dim) + tshape), lv, d, dim).reshape(E, nv, dim, Nfp)
-                    G = Gi + ph.eta * Li
-                    Gface[:, f] = G
-                    Fvis = ph.flux_vis(np.moveaxis(uf[:, f], 1, 0), np.transpose(G, (1, 2, 0, 3)))  # [nv, dim, E, Nfp]
-                    Fv_own[:, f] = np.moveaxis(np.einsum("vdef,efd->vef", Fvis, N[:, f]), 0, 1)
+                    Gface[:, f] = Gi + ph.eta * Li
+            for sel, ops in self.reduced:
+                Gface[sel] = mixed.face_gradients(m, ph, sel, ops, u, jmp)
+            for f in range(nf):
+                G = Gface[:, f]
+                Fvis = ph.flux_vis(np.moveaxis(uf[:, f], 1, 0), np.transpose(G, (1, 2, 0, 3)))  # [nv, dim, E, Nfp]
+                Fv_own[:, f] = np.moveaxis(np.einsum("vdef,efd->vef", Fvis, N[:, f]), 0, 1)
             Fv_common = np.zeros_like(Fv_own)
             Fv_common[ei, fi] = 0.5 * (Fv_own[ei, fi] - np.moveaxis(
                 Fv_own[ne[:, None], nfc[:, None], :, m.fpmap[ei, fi]], -1, 1))
@@ -196,12 +212,13 @@ class FRSolver:
         R = -div.reshape(E, nv, -1) / J[:, None]
         if self.source:
             R[:, nv - 1, :] += self.source_term(t)
-        if self.caps is not None:
-            from .sponge import project
-            R = project(m, R, self.caps)
+        red = []
+        for sel, ops in self.reduced:
+            R[sel], Rq, Jq = mixed.residual(m, ph, sel, ops, u, jmp, Fc)
+            red.append((sel, ops.q, Rq, Jq))
         if not want_faces:
             return R
-        return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc, "Gface": Gface}
+        return R, {"uf": uf, "Fv_common": Fv_common, "bc": bc, "Gface": Gface, "reduced": red}
 
     # -------------------------------------------------------------------
     def rk4_step(self, u, dt, t=0.0):

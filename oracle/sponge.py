@@ -1,21 +1,19 @@
-"""Variable polynomial order ("sponge zones", Section 3.1: a variable
-solution polynomial degree, P0 far from the body up to P3 or P4 near it, keeps
-acoustic waves from reflecting off the boundaries).
+"""Variable polynomial degree by element ("sponge zones", Section 3.1: a
+variable solution polynomial degree, P0 far from the body up to P3 or P4 near
+it, keeps acoustic waves from reflecting off the boundaries).
 
-Reading (the paper gives only the order distribution as a figure): every
-element carries the context's points of degree p; an element of order q < p
-keeps its solution in the tensor-product space of degree q.  Its residual is
-replaced by the L2 projection onto that space, R <- Pi_q R, with the 1D
-projection (GL quadrature, exact for these degrees)
+An element of degree q < p holds a polynomial of degree q in each direction,
+stored as its values at the degree-p points; its residual is that of a
+degree-q FR element (``oracle.mixed``).  A state set on such an element is
+first projected onto that space with the L2 projection applied along every
+direction (GL quadrature, exact for these degrees)
 
     Pi_q[i, j] = sum_{k <= q} P_k(x_i) P_k(x_j) w_j (2k + 1) / 2
 
-applied along every direction (P_k the Legendre polynomials, x, w the GL
-points and weights).  A state set on such an element is projected the same
-way, so the explicit update never leaves the space.  Pi_q keeps the element
-mean (k = 0), so affine elements stay conservative.
+(P_k the Legendre polynomials, x, w the degree-p GL points and weights).
+Pi_q keeps the element mean (k = 0).
 
-Test infrastructure (see ``oracle/__init__``).
+Test infrastructure (see ``oracle/__init``).
 """
 from __future__ import annotations
 
