@@ -229,18 +229,6 @@ def algorithmic_bytes(E, p, rsz, viscous=True, dim=3, curved=False):
     return {"traces": traces, "visc": visc, "resid": resid}
 
 
-def sponge_bytes(n, p, rsz, dim=3):
-    """Minimum HBM bytes per launch of the reduced-degree projection, stage
-    average: stages 1-3 read and write the stage output and the accumulator,
-    stage 4 the new state; every stage writes the projected state's traces and
-    reads the (element, degree) entry."""
-    np_ = p + 1
-    nsp, nfp, nf, nv = np_ ** dim, np_ ** (dim - 1), 2 * dim, dim + 2
-    u = nv * nsp * rsz
-    tr = nf * nv * nfp * rsz
-    return n * ((3 * 4 * u + 2 * u) / 4.0 + tr + 8)
-
-
 WORKLOADS = {
     "tgv32_p3": "3D Taylor-Green vortex Re=1600 M=0.1, periodic 32^3 hexes, FR p=3 (2,097,152 DOF), "
                 "Rusanov+BR2, RK4 dt=2.5e-4",
@@ -423,10 +411,19 @@ def gpu_leg(args, rank, world, local_rank):
 
     kernels = {"traces": kstat(0, "traces"), "visc_face": kstat(1, "visc"), "residual_rk": kstat(2, "resid")}
     if orders is not None:
+        # the reduced-degree elements run their own face and residual kernels:
+        # their time per element and stage against that of the full-degree
+        # elements (face + residual kernels)
         nred = int((orders < p).sum())
-        ab["sponge"] = sponge_bytes(nred, p, rsz)
-        kernels["sponge_projection"] = dict(kstat(5, "sponge"), elements=nred,
-                                            degrees=np.bincount(orders, minlength=p + 1).tolist())
+        stages = 4 * args.steps
+        red_ms = kms[5] / stages
+        full_ms = (kms[1] + kms[2]) / stages
+        kernels["reduced_degree"] = {
+            "avg_ms": kms[5] / max(kn[5], 1), "launches": int(kn[5]), "elements": nred,
+            "degrees": np.bincount(orders, minlength=p + 1).tolist(),
+            "dof_native": int(sum((int(q) + 1) ** 3 for q in orders)),
+            "us_per_element_stage": 1e3 * red_ms / max(nred, 1),
+            "full_degree_us_per_element_stage": 1e3 * full_ms / max(E - nred, 1)}
     u32 = F.fr_state_get(ctx)
     steps_done = args.warmup + 2 * args.steps
     # per-candidate wall forces accumulated over the same steps (C_L, C_D,

@@ -211,7 +211,8 @@ int fr_set_cand_dt(fr_ctx* ctx, int cand, double dt);
  *         below 1e-30 are skipped.
  *   t0    the candidate's time t_n from now on; every RK4 step advances it by
  *         the candidate's dt (fr_set_cand_dt or the options' dt).
- * Errors: FR_EINVAL (bad candidate, nsrc, non-finite values, k < 0),
+ * Errors: FR_EINVAL (bad candidate, nsrc, non-finite values, k < 0, a
+ * candidate with elements of reduced degree, fr_set_element_order),
  * FR_ENOMEM.  Rebuilds the step's CUDA graph on its next replay. */
 int fr_set_source(fr_ctx* ctx, int cand, int nsrc, const double* src, double t0);
 
@@ -240,17 +241,28 @@ int fr_cand_dt(const fr_ctx* ctx, int cand, double* dt);
  * context's p near the body to 0 in the outer rings, so that the coarse,
  * low-order far field absorbs outgoing waves).  order[i] in 0..p is the degree
  * of element i of candidate cand (cand = -1: of the whole batch, E entries);
- * order = NULL gives the candidate's elements p again.  Every element keeps
- * the context's (p+1)^dim points; an element of degree q < p holds its
- * solution in the tensor-product polynomials of degree q: its residual is
- * replaced by the L2 projection onto that space (the 1D projection
- *   Pi_q[i][j] = sum_{k<=q} P_k(x_i) P_k(x_j) w_j (2k+1)/2,
- * P_k Legendre, x, w the GL points and weights, along each direction), and
- * the current state and every state set later are projected the same way.
- * The projection keeps each element's mean, so conservation holds on affine
- * elements.  Errors: FR_EINVAL (cand out of range, an order outside 0..p),
- * FR_ENOMEM.  Synchronises the device; rebuilds the step's CUDA graph on its
- * next replay. */
+ * order = NULL gives the candidate's elements p again.  An element of degree
+ * q < p is a degree-q FR element on its own (q+1)^dim GL points, with the
+ * degree-q operators (at q = 0 the one linear correction function) and its
+ * metric terms taken as the degree-p interpolants evaluated at those points,
+ * while every face keeps the degree-p flux points, so faces stay conforming:
+ *   - its state is stored as the values of its degree-q polynomial at the
+ *     degree-p points (the current state and every state set later are
+ *     projected onto that space with the 1D L2 projection
+ *     Pi_q[i][j] = sum_{k<=q} P_k(x_i) P_k(x_j) w_j (2k+1)/2 along each
+ *     direction), so traces, sampling and state transfers are unchanged;
+ *   - the jump u_c - u_f and the common normal flux at the degree-p face
+ *     points reach it through the L2 projection onto degree q along each face
+ *     direction (a mortar that keeps each face's mean);
+ *   - its residual, computed at its q points, is evaluated at the degree-p
+ *     points; its BR2 face gradients, built at its q face points, likewise.
+ * With q = p this is the uniform scheme; the scheme stays conservative and
+ * keeps a free stream on affine elements.  Reduced elements are handled by
+ * their own kernels, so they cost degree-q work.  A candidate with an energy
+ * source (fr_set_source) keeps a uniform degree.  Errors: FR_EINVAL (cand out
+ * of range, an order outside 0..p, a candidate with a source), FR_ENOMEM.
+ * Synchronises the device; rebuilds the step's CUDA graph on its next
+ * replay. */
 int fr_set_element_order(fr_ctx* ctx, int cand, const int32_t* order);
 
 /* Same as fr_rk_step but replays a CUDA graph of one step (captured on first
@@ -379,7 +391,7 @@ int64_t fr_launch_count(const fr_ctx* ctx);
  * replays it nsteps times on stream (synchronising after each replay to read
  * the events) and returns the summed device time (ms) per kernel kind in
  * ms_out[0..5] = traces, viscous faces, residual+RK, forces/sampling, energy
- * source, reduced-degree projection, and their launch counts in n_out[0..5].
+ * source, reduced-degree elements, and their launch counts in n_out[0..5].
  * Advances the state exactly like fr_rk_step. */
 int fr_profile_step(fr_ctx* ctx, int nsteps, void* stream, double ms_out[6], int64_t n_out[6]);
 

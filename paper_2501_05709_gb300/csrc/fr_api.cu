@@ -100,6 +100,13 @@ struct fr_ctx {
     int sp_n = 0;                             // capped elements (0: none)
     int32_t *sp_elem = nullptr, *sp_cap = nullptr;  // device [sp_n]
     std::vector<int> sp_off;                  // [ncand + 1]: each candidate's slice of the list
+    // the reduced elements grouped by degree q < p for the kernels of frk::Red:
+    // device lists, metric terms at their q points, per-element degrees
+    int red_n[frk::MAXNP] = {0, 0, 0, 0, 0};
+    int32_t* red_elem[frk::MAXNP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* red_S[frk::MAXNP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* red_iJ[frk::MAXNP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    signed char* order_d = nullptr;           // device [E] (null: no reduced element)
     // non-finite state detection: nonfinite[c] != 0 once candidate c's state
     // held a NaN or an infinity at the end of a step (cleared by fr_state_set)
     int* nonfinite = nullptr;                 // device [ncand]
@@ -163,6 +170,7 @@ frk::Geo<Real> geo_of(const fr_ctx* c) {
     g.sN_fp = c->sN_fp;
     g.diag = c->diag;
     g.bnd = c->bnd;
+    g.order = c->order_d;
     return g;
 }
 
@@ -293,6 +301,77 @@ int L_resid(fr_ctx* c, const Real* u, const Real* uf, const frk::Stage<Real>& st
                        : frl::residual<Real, 3>(c->p, u, uf, fvn, c->E, op, ph, g, st, c->lc[2], s);
 }
 
+// the degree-q operators of the reduced elements (frk::Red): q = 0 takes the
+// one linear correction function (DG), whatever the context's kind
+template <typename Real>
+frk::Red<Real> red_of(const fr_ctx* c, int q) {
+    frk::Red<Real> r;
+    std::memset(r.Iqp, 0, sizeof(r.Iqp));
+    std::memset(r.Ipq, 0, sizeof(r.Ipq));
+    std::memset(r.Pqp, 0, sizeof(r.Pqp));
+    std::memset(r.D, 0, sizeof(r.D));
+    std::memset(r.lm, 0, sizeof(r.lm));
+    std::memset(r.lp, 0, sizeof(r.lp));
+    std::memset(r.hm, 0, sizeof(r.hm));
+    std::memset(r.hp, 0, sizeof(r.hp));
+    frg::Ref1D rq;
+    frg::build_ref(q, q > 0 ? c->kind : 0, rq);
+    const frg::Ref1D& rp = c->ref;
+    const int nq = q + 1, np = c->np;
+    double Lq[frk::MAXNP][frk::MAXNP], Lp[frk::MAXNP][frk::MAXNP], dL[frk::MAXNP];
+    for (int i = 0; i < nq; ++i) frg::legendre(q, rq.x[i], Lq[i], dL);
+    for (int j = 0; j < np; ++j) frg::legendre(q, rp.x[j], Lp[j], dL);
+    for (int i = 0; i < nq; ++i)
+        for (int j = 0; j < np; ++j) {
+            r.Iqp[i * frk::MAXNP + j] = Real(frg::lagrange(rp.x, np, j, rq.x[i]));
+            r.Ipq[j * frk::MAXNP + i] = Real(frg::lagrange(rq.x, nq, i, rp.x[j]));
+            double v = 0.0;
+            for (int k = 0; k <= q; ++k) v += Lq[i][k] * Lp[j][k] * rp.w[j] * (2 * k + 1) * 0.5;
+            r.Pqp[i * frk::MAXNP + j] = Real(v);
+        }
+    for (int i = 0; i < nq; ++i) {
+        for (int j = 0; j < nq; ++j) r.D[i * frk::MAXNP + j] = Real(rq.D[i][j]);
+        r.lm[i] = Real(rq.lm[i]);
+        r.lp[i] = Real(rq.lp[i]);
+        r.hm[i] = Real(rq.hm[i]);
+        r.hp[i] = Real(rq.hp[i]);
+    }
+    const int nsq = c->dim == 2 ? nq * nq : nq * nq * nq;
+    r.n = c->red_n[q];
+    r.elem = c->red_elem[q];
+    r.S = static_cast<const Real*>(c->red_S[q]);
+    r.iJ = static_cast<const Real*>(c->red_iJ[q]);
+    r.sS = int64_t(c->dim) * c->dim * nsq;
+    r.sJ = nsq;
+    return r;
+}
+
+template <typename Real>
+int L_red_face(fr_ctx* c, int q, const Real* u, const Real* uf, cudaStream_t s) {
+    if (c->red_n[q] <= 0) return 0;
+    const auto rd = red_of<Real>(c, q);
+    const auto& op = ops_ref<Real>(c);
+    const auto ph = phys_of<Real>(c);
+    const auto g = geo_of<Real>(c);
+    Real* fvn = static_cast<Real*>(c->fvn);
+    ++c->launches;
+    return c->dim == 2 ? frl::red_face<Real, 2>(c->p, q, rd, u, uf, fvn, op, ph, g, s)
+                       : frl::red_face<Real, 3>(c->p, q, rd, u, uf, fvn, op, ph, g, s);
+}
+
+template <typename Real>
+int L_red_resid(fr_ctx* c, int q, const Real* u, const Real* uf, const frk::Stage<Real>& st, cudaStream_t s) {
+    if (c->red_n[q] <= 0) return 0;
+    const auto rd = red_of<Real>(c, q);
+    const auto& op = ops_ref<Real>(c);
+    const auto ph = phys_of<Real>(c);
+    const auto g = geo_of<Real>(c);
+    const Real* fvn = static_cast<const Real*>(c->fvn);
+    ++c->launches;
+    return c->dim == 2 ? frl::red_resid<Real, 2>(c->p, q, rd, u, uf, fvn, op, ph, g, st, s)
+                       : frl::red_resid<Real, 3>(c->p, q, rd, u, uf, fvn, op, ph, g, st, s);
+}
+
 template <typename Real>
 int L_forces(fr_ctx* c, cudaStream_t s) {
     if (c->wall_off.empty() || c->wall_off.back() == 0) return 0;
@@ -408,6 +487,13 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             rc = L_visc<Real>(c, in, uf_in, s);
             if (pr) pr->mark_end();
             CKL(rc, "viscous face kernel");
+            for (int q = 0; q < c->p; ++q)
+                if (c->red_n[q] > 0) {
+                    if (pr) pr->mark_begin(5);
+                    rc = L_red_face<Real>(c, q, in, uf_in, s);
+                    if (pr) pr->mark_end();
+                    CKL(rc, "reduced-degree face kernel");
+                }
         }
         if (stage == 1) {
             if (pr) pr->mark_begin(3);
@@ -448,17 +534,18 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
         CKL(rc, "residual kernel");
+        for (int q = 0; q < c->p; ++q)
+            if (c->red_n[q] > 0) {
+                if (pr) pr->mark_begin(5);
+                rc = L_red_resid<Real>(c, q, in, uf_in, st, s);
+                if (pr) pr->mark_end();
+                CKL(rc, "reduced-degree residual kernel");
+            }
         if (c->src_nentry > 0) {
             if (pr) pr->mark_begin(4);
             rc = L_source<Real>(c, src_of<Real>(c, cfac), st, s);
             if (pr) pr->mark_end();
             CKL(rc, "source kernel");
-        }
-        if (c->sp_n > 0) {
-            if (pr) pr->mark_begin(5);
-            rc = stage == ns ? L_sponge<Real>(c, u0, nullptr, uf_out, s) : L_sponge<Real>(c, us, acc, uf_out, s);
-            if (pr) pr->mark_end();
-            CKL(rc, "sponge kernel");
         }
     }
     if (c->src_nentry > 0) {
@@ -480,6 +567,10 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     if (c->visc) {
         rc = L_visc<Real>(c, u, uf, s);
         CKL(rc, "viscous face kernel");
+        for (int q = 0; q < c->p; ++q) {
+            rc = L_red_face<Real>(c, q, u, uf, s);
+            CKL(rc, "reduced-degree face kernel");
+        }
     }
     frk::Stage<Real> st;
     st.stage = 0;
@@ -489,13 +580,13 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     st.u0 = st.us = st.acc = st.uf_next = nullptr;
     rc = L_resid<Real>(c, u, uf, st, s);
     CKL(rc, "residual kernel");
+    for (int q = 0; q < c->p; ++q) {
+        rc = L_red_resid<Real>(c, q, u, uf, st, s);
+        CKL(rc, "reduced-degree residual kernel");
+    }
     if (c->src_nentry > 0) {
         rc = L_source<Real>(c, src_of<Real>(c, 0.0), st, s);
         CKL(rc, "source kernel");
-    }
-    if (c->sp_n > 0) {
-        rc = L_sponge<Real>(c, R, nullptr, nullptr, s);
-        CKL(rc, "sponge kernel");
     }
     return FR_OK;
 }
@@ -571,6 +662,12 @@ void release(fr_ctx* c) {
                     c->hlen, c->cand_off_d, c->lam, c->sp_elem, c->sp_cap, c->nonfinite, c->ufb3};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (int q = 0; q < frk::MAXNP; ++q) {
+        void* rb[] = {c->red_elem[q], c->red_S[q], c->red_iJ[q]};
+        for (void* b : rb)
+            if (b) cudaFree(b);
+    }
+    if (c->order_d) cudaFree(c->order_d);
     for (auto& s : c->surf) {
         void* sb[] = {s.pe, s.pw, s.hist, s.count};
         for (void* b : sb)
@@ -1301,6 +1398,114 @@ int rebuild_sources(fr_ctx* c) {
     return FR_OK;
 }
 
+// host copy (as double) of n consecutive Reals of a device array
+int download_real(const fr_ctx* c, const void* d, int64_t off, int64_t n, double* out) {
+    if (n <= 0) return FR_OK;
+    if (c->prec == FR_FP64) {
+        if (cudaMemcpy(out, static_cast<const double*>(d) + off, size_t(n) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return FR_ECUDA;
+        return FR_OK;
+    }
+    std::vector<float> f(static_cast<size_t>(n));
+    if (cudaMemcpy(f.data(), static_cast<const float*>(d) + off, size_t(n) * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FR_ECUDA;
+    for (int64_t i = 0; i < n; ++i) out[i] = f[size_t(i)];
+    return FR_OK;
+}
+
+// in [np^dim] -> out [nq^dim]: M [nq][np] along every direction (direction 0 fastest)
+void interp_vol(int dim, int np, int nq, const double* M, const double* in, double* out) {
+    std::vector<double> a(in, in + (dim == 2 ? np * np : np * np * np)), b;
+    int n[3] = {np, np, dim == 3 ? np : 1};
+    for (int d = 0; d < dim; ++d) {
+        int m[3] = {n[0], n[1], n[2]};
+        m[d] = nq;
+        b.assign(size_t(m[0]) * m[1] * m[2], 0.0);
+        for (int i2 = 0; i2 < m[2]; ++i2)
+            for (int i1 = 0; i1 < m[1]; ++i1)
+                for (int i0 = 0; i0 < m[0]; ++i0) {
+                    const int o[3] = {i0, i1, i2};
+                    double acc = 0.0;
+                    for (int j = 0; j < n[d]; ++j) {
+                        int ii[3] = {i0, i1, i2};
+                        ii[d] = j;
+                        acc += M[o[d] * frk::MAXNP + j] * a[(size_t(ii[2]) * n[1] + ii[1]) * n[0] + ii[0]];
+                    }
+                    b[(size_t(i2) * m[1] + i1) * m[0] + i0] = acc;
+                }
+        a.swap(b);
+        n[d] = nq;
+    }
+    std::copy(a.begin(), a.end(), out);
+}
+
+// The reduced-element tables of the kernels of frk::Red from c->order: per
+// degree q < p the element list and the metric terms at the q points (the
+// degree-p interpolants of S and |J| evaluated there, 1/|J| stored), and the
+// per-element degrees.
+int build_reduced(fr_ctx* c) {
+    for (int q = 0; q < frk::MAXNP; ++q) {
+        void* rb[] = {c->red_elem[q], c->red_S[q], c->red_iJ[q]};
+        for (void* b : rb)
+            if (b) cudaFree(b);
+        c->red_elem[q] = nullptr;
+        c->red_S[q] = c->red_iJ[q] = nullptr;
+        c->red_n[q] = 0;
+    }
+    if (c->order_d) cudaFree(c->order_d);
+    c->order_d = nullptr;
+    const int dim = c->dim, np = c->np, nsp = c->nsp;
+    std::vector<std::vector<int32_t>> lists(size_t(c->p));
+    std::vector<signed char> ord(size_t(c->E), static_cast<signed char>(c->p));
+    bool any = false;
+    for (int k = 0; k < c->ncand; ++k)
+        for (size_t i = 0; i < c->order[k].size(); ++i)
+            if (c->order[k][i] < c->p) {
+                const int64_t e = c->cand_off[k] + int64_t(i);
+                lists[size_t(c->order[k][i])].push_back(int32_t(e));
+                ord[size_t(e)] = static_cast<signed char>(c->order[k][i]);
+                any = true;
+            }
+    if (!any) return FR_OK;
+    int rc;
+    if ((rc = upload(reinterpret_cast<void**>(&c->order_d), ord))) return rc;
+    std::vector<double> Se(static_cast<size_t>(dim) * dim * nsp), Je(static_cast<size_t>(nsp)),
+        tmp(static_cast<size_t>(dim) * dim + 1);
+    for (int q = 0; q < c->p; ++q) {
+        const auto& el = lists[size_t(q)];
+        if (el.empty()) continue;
+        const int nq = q + 1, nsq = dim == 2 ? nq * nq : nq * nq * nq;
+        const auto rd = red_of<double>(c, q);
+        std::vector<double> Sq(el.size() * size_t(dim) * dim * nsq), iJq(el.size() * size_t(nsq));
+        for (size_t k = 0; k < el.size(); ++k) {
+            const int64_t e = el[k];
+            // S[e*sS_e + kk*sS_k + sp*sS_sp] and J[e*sJ_e + sp*sJ_sp] (stride 0: affine)
+            if (c->sS_sp == 0) {
+                if ((rc = download_real(c, c->S, e * c->sS_e, int64_t(dim) * dim, tmp.data()))) return rc;
+                for (int kk = 0; kk < dim * dim; ++kk)
+                    for (int sp = 0; sp < nsp; ++sp) Se[size_t(kk) * nsp + sp] = tmp[size_t(kk)];
+            } else {
+                if ((rc = download_real(c, c->S, e * c->sS_e, int64_t(dim) * dim * nsp, Se.data()))) return rc;
+            }
+            if (c->sJ_sp == 0) {
+                if ((rc = download_real(c, c->J, e * c->sJ_e, 1, tmp.data()))) return rc;
+                std::fill(Je.begin(), Je.end(), tmp[0]);
+            } else {
+                if ((rc = download_real(c, c->J, e * c->sJ_e, nsp, Je.data()))) return rc;
+            }
+            for (int kk = 0; kk < dim * dim; ++kk)
+                interp_vol(dim, np, nq, rd.Iqp, Se.data() + size_t(kk) * nsp, Sq.data() + (k * dim * dim + kk) * nsq);
+            interp_vol(dim, np, nq, rd.Iqp, Je.data(), iJq.data() + k * nsq);
+            for (int pt = 0; pt < nsq; ++pt) iJq[k * nsq + pt] = 1.0 / iJq[k * nsq + pt];
+        }
+        if ((rc = upload(reinterpret_cast<void**>(&c->red_elem[q]), el)) ||
+            (rc = upload_real(&c->red_S[q], Sq, c->prec)) || (rc = upload_real(&c->red_iJ[q], iJq, c->prec)))
+            return rc;
+        c->red_n[q] = int(el.size());
+    }
+    return FR_OK;
+}
+
 }  // namespace
 
 extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, double t0) {
@@ -1315,6 +1520,9 @@ extern "C" int fr_set_source(fr_ctx* c, int cand, int nsrc, const double* src, d
         }
     for (const auto& v : sv)
         if (!(v[1] >= 0.0)) return fail(FR_EINVAL, "source range factor k must be >= 0");
+    if (nsrc > 0 && !c->order.empty())
+        for (int32_t q : c->order[cand])
+            if (q < c->p) return fail(FR_EINVAL, "the energy source needs a candidate of uniform degree");
     CK(cudaDeviceSynchronize());
     if (!c->tnow) {
         const size_t nc = size_t(c->ncand);
@@ -1345,6 +1553,12 @@ extern "C" int fr_set_element_order(fr_ctx* c, int cand, const int32_t* order) {
         const int64_t n = c->cand_off[k1] - c->cand_off[k0];
         for (int64_t i = 0; i < n; ++i)
             if (order[i] < 0 || order[i] > c->p) return fail(FR_EINVAL, "element order outside 0..p");
+        for (int k = k0; k < k1; ++k) {
+            if (c->srcs.empty() || c->srcs[k].empty()) continue;
+            for (int64_t e = c->cand_off[k]; e < c->cand_off[k + 1]; ++e)
+                if (order[e - c->cand_off[k0]] < c->p)
+                    return fail(FR_EINVAL, "the energy source needs a candidate of uniform degree");
+        }
     }
     CK(cudaDeviceSynchronize());
     if (c->order.empty()) c->order.resize(c->ncand);
@@ -1376,7 +1590,7 @@ extern "C" int fr_set_element_order(fr_ctx* c, int cand, const int32_t* order) {
         CK(cudaMemcpy(c->sp_elem, el.data(), bytes, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->sp_cap, cp.data(), bytes, cudaMemcpyHostToDevice));
         c->sp_n = int(el.size());
-        // the current state of the changed candidates moves into the capped spaces
+        // the current state of the changed candidates moves into the reduced spaces
         for (int k = k0; k < k1; ++k) {
             const int rc = c->prec == FR_FP64
                                ? L_sponge<double>(c, static_cast<double*>(c->u0), nullptr, nullptr, nullptr, k)
@@ -1384,6 +1598,9 @@ extern "C" int fr_set_element_order(fr_ctx* c, int cand, const int32_t* order) {
             CKL(rc, "sponge kernel");
         }
     }
+    CK(cudaDeviceSynchronize());
+    const int rc = build_reduced(c);
+    if (rc) return fail(rc, "cannot build the reduced-degree element tables");
     c->traces_valid = false;
     invalidate_graph(c);
     CK(cudaDeviceSynchronize());

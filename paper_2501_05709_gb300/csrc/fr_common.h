@@ -58,6 +58,10 @@ struct Geo {
     int diag;
     // 1: some element face lies on a boundary (0: fully periodic mesh)
     int bnd;
+    // per-element polynomial degree when some element has a reduced degree
+    // (null: every element has the mesh's degree); the element kernels of the
+    // mesh's degree skip the reduced ones, which the kernels of Red handle
+    const signed char* order = nullptr;
 };
 
 // Stage control for the fused residual/update kernel.  Classic RK4 (ls = 0):
@@ -142,6 +146,25 @@ struct Sponge {
     Real pm[MAXNP][MAXNP * MAXNP];
 };
 
+// Elements of reduced degree Q < P inside a degree-P mesh (variable solution
+// degree, Section 3.1): the n listed elements elem[k], their metric terms at
+// the Q points S[k*sS + (d*DIM + i)*NSQ + pt] and 1/|J| iJ[k*sJ + pt] (the
+// degree-P interpolants of the element's metrics evaluated there), and the
+// degree-Q operators (row-major, row stride MAXNP): Iqp [NQ][NP] the
+// Lagrange basis of the P points at the Q points, Ipq [NP][NQ] the reverse,
+// Pqp [NQ][NP] the L2 projection onto degree Q (values at the Q points), D
+// the degree-Q derivative matrix, lm/lp and hm/hp as in Ops for degree Q.
+template <typename Real>
+struct Red {
+    int n = 0;
+    const int32_t* elem = nullptr;
+    const Real* S = nullptr;
+    const Real* iJ = nullptr;
+    int64_t sS = 0, sJ = 0;
+    Real Iqp[MAXNP * MAXNP], Ipq[MAXNP * MAXNP], Pqp[MAXNP * MAXNP], D[MAXNP * MAXNP];
+    Real lm[MAXNP], lp[MAXNP], hm[MAXNP], hp[MAXNP];
+};
+
 }  // namespace frk
 
 // Host-side launchers implemented per precision and dimension.
@@ -200,6 +223,18 @@ int cfl(int P, const Real* u, const Real* hlen, int64_t E, const int64_t* cand_o
 int residual_tc3(int P, int opm, const float* u, const float* uf, const float* fvn, int64_t E,
                  const frk::Ops<float>& op, const frk::Phys<float>& ph, const frk::Geo<float>& g,
                  const frk::Stage<float>& st, frk::Launch lc, void* stream);
+
+// the reduced-degree elements of Red (degree Q < P): BR2 face gradients and
+// own viscous normal fluxes (red_face, viscous meshes), and the residual with
+// the stage update and next traces (red_resid)
+template <typename Real, int DIM>
+int red_face(int P, int Q, const frk::Red<Real>& rd, const Real* u, const Real* uf, Real* fvn,
+             const frk::Ops<Real>& op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g, void* stream);
+
+template <typename Real, int DIM>
+int red_resid(int P, int Q, const frk::Red<Real>& rd, const Real* u, const Real* uf, const Real* fvn,
+              const frk::Ops<Real>& op, const frk::Phys<Real>& ph, const frk::Geo<Real>& g,
+              const frk::Stage<Real>& st, void* stream);
 
 // threads per element of the element kernels (32 or 64; at 64 an element
 // group synchronises on a named barrier, so a block holds at most 15 groups)

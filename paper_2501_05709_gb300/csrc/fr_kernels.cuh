@@ -1080,6 +1080,7 @@ __global__ void k_visc_face_aff(
         int codes[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mine, f);
+        if (g.order && g.order[el] < P) return;   // a reduced-degree element (k_red_face)
         warp_stage_vol<DIM, P>(b, u + el * NV * NSP, lane, T);
         warp_stage<NF * NV * NFP, VS>(b + SM::pl, uf + el * NF * NV * NFP, lane, T);
 #pragma unroll
@@ -1110,8 +1111,9 @@ __global__ void k_visc_face_aff(
         int codes[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) codes[f] = __shfl_sync(0xffffffffu, mineA, f);
-        visc_faces_affine<DIM, P, Real, MP == 2, BND, VS>(cur, cur + SM::pl, cur + SM::pn, cur + SM::pg, codes, e,
-                                                          fvn, op, ph, lane);
+        if (!g.order || g.order[e] >= P)
+            visc_faces_affine<DIM, P, Real, MP == 2, BND, VS>(cur, cur + SM::pl, cur + SM::pn, cur + SM::pg, codes,
+                                                              e, fvn, op, ph, lane);
         if (en >= E) break;
         grp_sync<T>(grp);   // every thread is done with cur before it is refilled
         e = en;
@@ -1142,7 +1144,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x / T, lane = threadIdx.x % T;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
-    if (e >= E) return;
+    if (e >= E || (g.order && g.order[e] < P)) return;   // reduced: k_red_*
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
     constexpr bool curved = MP == 0;                // per-point metrics, staged after region D
@@ -1370,7 +1372,7 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x / T, lane = threadIdx.x % T;
     const int64_t e = int64_t(blockIdx.x) * (blockDim.x / T) + warp;
-    if (e >= E) return;
+    if (e >= E || (g.order && g.order[e] < P)) return;   // reduced: k_red_*
     using SM = Smem<DIM, P>;
     using VL = Vol<DIM, P, Real>;
     constexpr bool curved = MP == 0;                // per-point metrics, staged in region E

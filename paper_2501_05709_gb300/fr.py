@@ -421,7 +421,7 @@ def fr_probe_fp64_peak(stream=None):
 
 def fr_profile_step(ctx, nsteps, stream=None):
     """(ms [6], launches [6]) per kernel kind: traces, viscous faces, residual+RK, forces/sampling,
-    energy source, reduced-degree projection."""
+    energy source, reduced-degree elements (their face and residual kernels)."""
     ms = np.zeros(6)
     n = np.zeros(6, dtype=np.int64)
     _check(lib().fr_profile_step(ctx.handle, int(nsteps), _stream(stream), _ptr(ms), _ptr(n)))

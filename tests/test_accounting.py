@@ -32,12 +32,6 @@ def test_algorithmic_bytes_per_element(bench):
     assert bench.algorithmic_bytes(7, 3, 4)["resid"] == 7 * bench.algorithmic_bytes(1, 3, 4)["resid"]
 
 
-def test_sponge_bytes(bench):
-    # stage arrays read and written (3.5 states on average), traces written, the list entry
-    assert bench.sponge_bytes(1, 3, 4) == 6408
-    assert bench.sponge_bytes(10, 3, 4) == 64080
-
-
 def test_sponge_degrees_of_the_ogrid():
     from paper_2501_05709_gb300 import workloads as W
     nodes, _ = W.ogrid_mesh(40, 20, 1, 0.2, r_outer=10.0, first_cell=2e-2)

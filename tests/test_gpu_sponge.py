@@ -1,7 +1,8 @@
-"""GPU parity of variable polynomial order by element (the sponge zones of
-Section 3.1) through the C-ABI, against the oracle's projection reading:
-residual, state projection, RK4 steps, graph replay, per-candidate orders,
-removal, conservation and the FP32 bound."""
+"""GPU parity of variable polynomial degree by element (the sponge zones of
+Section 3.1: degree-q elements with faces at the degree-p points) through the
+C-ABI, against the oracle: residual, state projection, RK4 steps, graph
+replay, per-candidate degrees, removal, conservation, the Euler path, the FP32
+bound, and that the reduced elements run their own kernels."""
 import numpy as np
 import pytest
 
@@ -210,3 +211,74 @@ def test_orders_fp32_bound():
         torch.cuda.synchronize()
         R = Rd.double().cpu().numpy()
     assert relerr(R, s.residual(u)) <= 1e-5
+
+
+def test_euler_with_orders_fp64():
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("euler3d_ogrid_p2")
+    E = len(c["conn"])
+    caps = _caps(E, c["p"], seed=23)
+    m, s = _oracle(c, caps)
+    u = c["state"](m.xsp)
+    R_or = s.residual(u)
+    with F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c)) as ctx:
+        F.fr_set_element_order(ctx, caps)
+        ud = torch.tensor(u, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.cpu().numpy()
+    assert relerr(R, R_or) <= fp64_tol(s.residual, u)
+
+
+def test_reduced_elements_run_their_own_kernels():
+    # per RK stage one face and one residual launch per reduced degree present
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("ns3d_curved_p3")
+    E = len(c["conn"])
+    caps = _caps(E, c["p"], seed=29)
+    m, _ = _oracle(c, None)
+    u = c["state"](m.xsp)
+    with F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c)) as ctx:
+        F.fr_state_set(ctx, u)
+        _, n0 = F.fr_profile_step(ctx, 1)
+        F.fr_set_element_order(ctx, caps)
+        F.fr_state_set(ctx, u)
+        _, n1 = F.fr_profile_step(ctx, 1)
+    nq = len(set(int(q) for q in caps) - {c["p"]})
+    assert n0[5] == 0 and n1[5] == 4 * 2 * nq
+    assert n1[2] == n0[2] == 4
+
+
+def test_source_needs_a_uniform_degree():
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("ns3d_p1")
+    E = len(c["conn"])
+    caps = _caps(E, c["p"], seed=31)
+    with F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c)) as ctx:
+        F.fr_set_element_order(ctx, caps)
+        with pytest.raises(F.FrError) as e:
+            F.fr_set_source(ctx, 0, [(1.0, 10.0, (0.5, 0.5, 0.5), 2.0)])
+        assert e.value.code == F.FR_EINVAL
+        F.fr_set_element_order(ctx, None)
+        F.fr_set_source(ctx, 0, [(1.0, 10.0, (0.5, 0.5, 0.5), 2.0)])
+        with pytest.raises(F.FrError) as e:
+            F.fr_set_element_order(ctx, caps)
+        assert e.value.code == F.FR_EINVAL
+
+
+def test_tensor_core_mode_with_orders():
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("ns3d_curved_p3")
+    E = len(c["conn"])
+    caps = _caps(E, c["p"], seed=37)
+    m, s = _oracle(c, caps)
+    u = c["state"](m.xsp)
+    with F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c, precision=F.FR_BF16X3_TC)) as ctx:
+        F.fr_set_element_order(ctx, caps)
+        ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+    assert relerr(R, s.residual(u)) <= 1e-3
