@@ -74,6 +74,11 @@ struct fr_ctx {
     std::vector<Surface> surf;
     frk::Launch lc[3]{};
     cudaStream_t cap_stream = nullptr;
+    // the reduced-degree kernels of a step run on red_stream, forked from the
+    // step's stream and joined back (they write only the reduced elements'
+    // arrays, the degree-p kernels only the others')
+    cudaStream_t red_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
     int64_t graph_launches_per_step = 0;
@@ -458,6 +463,20 @@ int enqueue_adaptive_dt(fr_ctx* c, cudaStream_t s) {
     return FR_OK;
 }
 
+// red_stream waits for the work enqueued on s so far; s later waits for the
+// work enqueued on red_stream (inside a stream capture both become graph
+// dependencies)
+cudaError_t fork_red(fr_ctx* c, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->red_stream, c->ev_fork, 0);
+    return e;
+}
+cudaError_t join_red(fr_ctx* c, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(c->ev_join, c->red_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    return e;
+}
+
 template <typename Real>
 int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
     Real* u0 = static_cast<Real*>(c->u0);
@@ -477,12 +496,18 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         if (ns % 2 == 0) return static_cast<Real*>(c->ufb[st & 1]);
         return static_cast<Real*>(st & 1 ? c->ufb[1] : c->ufb3);
     };
+    // reduced-degree kernels beside the degree-p ones (not when every launch
+    // is timed on its own)
+    bool fork = false;
+    for (int q = 0; q < c->p; ++q) fork = fork || c->red_n[q] > 0;
+    fork = fork && !pr;
     for (int stage = 1; stage <= ns; ++stage) {
         const Real* in = (stage == 1) ? u0 : us;
         const Real* uf_in = trace_buf(stage - 1);
         Real* uf_out = trace_buf(stage);
         int rc;
         if (c->visc) {
+            if (fork) CK(fork_red(c, s));
             if (pr) pr->mark_begin(1);
             rc = L_visc<Real>(c, in, uf_in, s);
             if (pr) pr->mark_end();
@@ -490,10 +515,11 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             for (int q = 0; q < c->p; ++q)
                 if (c->red_n[q] > 0) {
                     if (pr) pr->mark_begin(5);
-                    rc = L_red_face<Real>(c, q, in, uf_in, s);
+                    rc = L_red_face<Real>(c, q, in, uf_in, fork ? c->red_stream : s);
                     if (pr) pr->mark_end();
                     CKL(rc, "reduced-degree face kernel");
                 }
+            if (fork) CK(join_red(c, s));
         }
         if (stage == 1) {
             if (pr) pr->mark_begin(3);
@@ -530,6 +556,7 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             st.cf = Real(k[5]);
             cfac = c->ls_time[stage - 1];
         }
+        if (fork) CK(fork_red(c, s));
         if (pr) pr->mark_begin(2);
         rc = L_resid<Real>(c, in, uf_in, st, s);
         if (pr) pr->mark_end();
@@ -537,10 +564,11 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         for (int q = 0; q < c->p; ++q)
             if (c->red_n[q] > 0) {
                 if (pr) pr->mark_begin(5);
-                rc = L_red_resid<Real>(c, q, in, uf_in, st, s);
+                rc = L_red_resid<Real>(c, q, in, uf_in, st, fork ? c->red_stream : s);
                 if (pr) pr->mark_end();
                 CKL(rc, "reduced-degree residual kernel");
             }
+        if (fork) CK(join_red(c, s));
         if (c->src_nentry > 0) {
             if (pr) pr->mark_begin(4);
             rc = L_source<Real>(c, src_of<Real>(c, cfac), st, s);
@@ -675,6 +703,9 @@ void release(fr_ctx* c) {
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->red_stream) cudaStreamDestroy(c->red_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -1030,7 +1061,10 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         return fail(FR_ENOMEM, "cudaMalloc failed for the non-finite flags");
     }
     cudaMemset(c->nonfinite, 0, sizeof(int) * ncand);
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->red_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         release(c);
         return fail(FR_ECUDA, "cannot create a stream");
     }

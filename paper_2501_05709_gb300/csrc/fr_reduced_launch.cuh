@@ -21,11 +21,12 @@ int red_face_pq(const frk::Red<FR_REAL>& rd, const FR_REAL* u, const FR_REAL* uf
                 cudaStream_t s) {
     auto k = frk::k_red_face<FR_DIM, P, Q, FR_REAL>;
     constexpr size_t sm = frk::smem_red<FR_DIM, P, Q, FR_REAL>(true);
+    constexpr int W = frk::red_w<FR_DIM, P, Q, FR_REAL>(true);
     static bool done = false;
     const cudaError_t e = red_prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (rd.n <= 0) return 0;
-    k<<<unsigned(rd.n), 32, sm, s>>>(rd, u, uf, fvn, op, ph, g);
+    k<<<unsigned((rd.n + W - 1) / W), 32 * W, sm, s>>>(rd, u, uf, fvn, op, ph, g);
     return int(cudaGetLastError());
 }
 
@@ -35,11 +36,12 @@ int red_resid_pq(const frk::Red<FR_REAL>& rd, const FR_REAL* u, const FR_REAL* u
                  const frk::Stage<FR_REAL>& st, cudaStream_t s) {
     auto k = frk::k_red_resid<FR_DIM, P, Q, FR_REAL, V>;
     constexpr size_t sm = frk::smem_red<FR_DIM, P, Q, FR_REAL>(false);
+    constexpr int W = frk::red_w<FR_DIM, P, Q, FR_REAL>(false);
     static bool done = false;
     const cudaError_t e = red_prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (rd.n <= 0) return 0;
-    k<<<unsigned(rd.n), 32, sm, s>>>(rd, u, uf, fvn, op, ph, g, st);
+    k<<<unsigned((rd.n + W - 1) / W), 32 * W, sm, s>>>(rd, u, uf, fvn, op, ph, g, st);
     return int(cudaGetLastError());
 }
 

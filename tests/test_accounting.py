@@ -44,3 +44,22 @@ def test_sponge_degrees_of_the_ogrid():
     # never rises with the distance from the body
     order = np.argsort(r)
     assert np.all(np.diff(q[order]) <= 0)
+
+
+def test_reduced_bytes_per_element(bench):
+    # a reduced element moves a degree-p element's arrays (state, traces,
+    # viscous fluxes, RK arrays at the degree-p points) with the metric terms
+    # (S and 1/|J|, 10 values per point in 3D) at its (q+1)^3 points, in each
+    # of its two kernels
+    full = bench.algorithmic_bytes(1, 3, 4, viscous=True, curved=True)
+    for q in range(3):
+        r = bench.reduced_bytes([q], 3, 4, viscous=True, curved=True)
+        assert r == full["visc"] + full["resid"] - 2 * 10 * (64 - (q + 1) ** 3) * 4
+    # Euler on an affine mesh: no face kernel, no viscous-flux array; a
+    # degree-p element holds one metric set, a reduced one a set per q point
+    e = bench.algorithmic_bytes(1, 3, 4, viscous=False, curved=False)
+    assert bench.reduced_bytes([1], 3, 4, viscous=False) == e["resid"] + 10 * (8 - 1) * 4
+    # degree-p elements are not counted; additive over elements
+    assert bench.reduced_bytes([3, 3], 3, 4) == 0
+    assert bench.reduced_bytes([0, 1, 1, 3], 3, 4) == (bench.reduced_bytes([0], 3, 4)
+                                                       + 2 * bench.reduced_bytes([1], 3, 4))
