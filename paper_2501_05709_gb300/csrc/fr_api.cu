@@ -74,11 +74,11 @@ struct fr_ctx {
     std::vector<Surface> surf;
     frk::Launch lc[3]{};
     cudaStream_t cap_stream = nullptr;
-    // the reduced-degree kernels of a step run on red_stream, forked from the
-    // step's stream and joined back (they write only the reduced elements'
-    // arrays, the degree-p kernels only the others')
-    cudaStream_t red_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the reduced-degree kernels of a step run on red_stream[q] (one per
+    // degree q), forked from the step's stream and joined back (they write
+    // only the reduced elements' arrays, the degree-p kernels only the others')
+    cudaStream_t red_stream[frk::MAXNP] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[frk::MAXNP] = {};
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
     int64_t graph_launches_per_step = 0;
@@ -463,17 +463,22 @@ int enqueue_adaptive_dt(fr_ctx* c, cudaStream_t s) {
     return FR_OK;
 }
 
-// red_stream waits for the work enqueued on s so far; s later waits for the
-// work enqueued on red_stream (inside a stream capture both become graph
+// the red streams wait for the work enqueued on s so far; s later waits for
+// the work enqueued on them (inside a stream capture both become graph
 // dependencies)
 cudaError_t fork_red(fr_ctx* c, cudaStream_t s) {
     cudaError_t e = cudaEventRecord(c->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->red_stream, c->ev_fork, 0);
+    for (int q = 0; q < c->p && e == cudaSuccess; ++q)
+        if (c->red_n[q] > 0) e = cudaStreamWaitEvent(c->red_stream[q], c->ev_fork, 0);
     return e;
 }
 cudaError_t join_red(fr_ctx* c, cudaStream_t s) {
-    cudaError_t e = cudaEventRecord(c->ev_join, c->red_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < c->p && e == cudaSuccess; ++q)
+        if (c->red_n[q] > 0) {
+            e = cudaEventRecord(c->ev_join[q], c->red_stream[q]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[q], 0);
+        }
     return e;
 }
 
@@ -515,7 +520,7 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             for (int q = 0; q < c->p; ++q)
                 if (c->red_n[q] > 0) {
                     if (pr) pr->mark_begin(5);
-                    rc = L_red_face<Real>(c, q, in, uf_in, fork ? c->red_stream : s);
+                    rc = L_red_face<Real>(c, q, in, uf_in, fork ? c->red_stream[q] : s);
                     if (pr) pr->mark_end();
                     CKL(rc, "reduced-degree face kernel");
                 }
@@ -564,7 +569,7 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         for (int q = 0; q < c->p; ++q)
             if (c->red_n[q] > 0) {
                 if (pr) pr->mark_begin(5);
-                rc = L_red_resid<Real>(c, q, in, uf_in, st, fork ? c->red_stream : s);
+                rc = L_red_resid<Real>(c, q, in, uf_in, st, fork ? c->red_stream[q] : s);
                 if (pr) pr->mark_end();
                 CKL(rc, "reduced-degree residual kernel");
             }
@@ -703,9 +708,11 @@ void release(fr_ctx* c) {
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    if (c->red_stream) cudaStreamDestroy(c->red_stream);
+    for (int q = 0; q < frk::MAXNP; ++q) {
+        if (c->red_stream[q]) cudaStreamDestroy(c->red_stream[q]);
+        if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
+    }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -1061,10 +1068,12 @@ extern "C" int fr_mesh_load(const fr_mesh_desc* m, int ncand, const fr_options* 
         return fail(FR_ENOMEM, "cudaMalloc failed for the non-finite flags");
     }
     cudaMemset(c->nonfinite, 0, sizeof(int) * ncand);
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->red_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    bool streams_ok = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int q = 0; q < c->p && streams_ok; ++q)
+        streams_ok = cudaStreamCreateWithFlags(&c->red_stream[q], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming) == cudaSuccess;
+    if (!streams_ok) {
         release(c);
         return fail(FR_ECUDA, "cannot create a stream");
     }
