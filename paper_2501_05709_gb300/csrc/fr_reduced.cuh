@@ -9,18 +9,18 @@
 // mortar), and its residual, evaluated at its Q points with degree-Q
 // operators, goes back to the degree-P points as the polynomial it is.
 //
-// One warp per element, RedSz::W elements per block.  Every input of the
-// element (state, own and neighbour traces, own and neighbour viscous
-// fluxes, metric terms at the Q points) is staged into shared memory by
-// cp.async at kernel start, and the face normals of the lane's face points
-// and the RK stage arrays of its final points are loaded into registers
-// there too, so the element pays one memory latency.  Every operator is
-// applied along lines: a lane takes one line (or one face array), holds its
-// values in registers and forms all outputs of the line with operator
-// indices that are compile-time after unrolling, so the operator entries
-// come from the constant bank of the __grid_constant__ parameters.  Shared
-// arrays use the canonical layouts (point i0 + N i1 + N^2 i2, face point
-// a + N b with a the lower of the face's two directions).
+// One warp per element, red_w elements per block.  The element's state is
+// staged into shared memory by cp.async at kernel start; the face data (own
+// and neighbour traces and viscous fluxes, normals), the metric terms at the
+// Q points and the RK stage arrays are read from global memory where they
+// are used, which keeps shared memory near 8 KB per element (FP32, P = 3).
+// Every operator is applied along lines: a lane takes one line (or one face
+// array), holds its values in registers and forms all outputs of the line
+// with operator indices that are compile-time after unrolling, so the
+// operator entries come from the constant bank of the __grid_constant__
+// parameters.  Volume arrays in shared memory use the canonical layout
+// (point i0 + N i1 + N^2 i2); face rows (face point a + N b, a the lower of
+// the face's two directions) are padded to an odd stride.
 #pragma once
 
 #include <type_traits>
