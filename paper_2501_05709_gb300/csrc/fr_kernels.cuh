@@ -1328,23 +1328,18 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
             }
             const Real* N = Nr[d][it];
             const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
-            Real Fv[NV][DIM];
+            Real Fn[NV];
             if (!BND || code >= 0) {
-                visc_flux<DIM>(uL, G, ph.mu, ph.kappa, Fv);
+                visc_flux_n<DIM>(uL, G, ph.mu, ph.kappa, N, Fn);
             } else {
                 Real ug[NV], ub[NV];
                 bc_state<DIM>(-code, uL, N, ph, ug, ub);
-                visc_flux<DIM>(ub, G, ph.mu, ph.kappa, Fv);
+                visc_flux_n<DIM>(ub, G, ph.mu, ph.kappa, N, Fn);
+                if (code == -FR_BC_WALL) Fn[NV - 1] = Real(0);
             }
             Real* dst = fvn + (e * NF + f) * NV * NFP + fp;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                Real acc = Real(0);
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) acc += Fv[v][i] * N[i];
-                if (v == NV - 1 && code == -FR_BC_WALL) acc = Real(0);
-                dst[v * NFP] = acc;
-            }
+            for (int v = 0; v < NV; ++v) dst[v * NFP] = Fn[v];
         }
     }
     }
