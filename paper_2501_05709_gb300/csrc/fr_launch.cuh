@@ -14,11 +14,17 @@ namespace {
 // `done` belongs to the caller's own kernel instantiation (kernels of
 // different orders share a signature, so the flag cannot live here).
 template <typename K>
-cudaError_t prep(K kernel, size_t smem, bool& done) {
+cudaError_t prep(K kernel, size_t smem, unsigned long long& done) {
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess) done = true;
+    // the attribute belongs to the function on the current device: one bit
+    // of `done` per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) done |= bit;
     return e;
 }
 
@@ -29,7 +35,7 @@ int traces_p(const FR_REAL* u, FR_REAL* uf, int64_t E, const frk::Ops<FR_REAL>& 
              cudaStream_t s) {
     auto k = frk::k_traces<FR_DIM, P, FR_REAL>;
     const size_t sm = frk::smem_traces<FR_DIM, P, FR_REAL>(lc.epb);
-    static bool done = false;
+    static unsigned long long done = 0;
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;
@@ -58,7 +64,7 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
     if constexpr (MP == 0) {
         auto k = frk::k_visc_face<FR_DIM, P, FR_REAL, MP, BND>;
         const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, true);
-        static bool done = false;
+        static unsigned long long done = 0;
         cudaError_t e = prep(k, sm, done);
         if (e != cudaSuccess) return int(e);
         if (E == 0) return 0;
@@ -70,7 +76,7 @@ int visc_p(const FR_REAL* u, const FR_REAL* uf, FR_REAL* fvn, int64_t E, const f
         // empty launch at mesh load, outside any stream capture)
         auto k = frk::k_visc_face_aff<FR_DIM, P, FR_REAL, MP, BND>;
         const size_t sm = frk::smem_visc<FR_DIM, P, FR_REAL>(lc.epb, false);
-        static bool done = false;
+        static unsigned long long done = 0;
         static int regs = 0, nsm = 0;
         cudaError_t e = prep(k, sm, done);
         if (e != cudaSuccess) return int(e);
@@ -95,7 +101,7 @@ int resid_p(const FR_REAL* u, const FR_REAL* uf, const FR_REAL* fvn, int64_t E,
             const frk::Stage<FR_REAL>& st, frk::Launch lc, cudaStream_t s) {
     auto k = frk::k_residual<FR_DIM, P, FR_REAL, MP, VISC, BND>;
     const size_t sm = frk::smem_resid<FR_DIM, P, FR_REAL>(lc.epb, g.sS_sp != 0);
-    static bool done = false;
+    static unsigned long long done = 0;
     cudaError_t e = prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;

@@ -7,11 +7,17 @@ namespace frl {
 namespace {
 
 template <typename K>
-cudaError_t red_prep(K kernel, size_t smem, bool& done) {
+cudaError_t red_prep(K kernel, size_t smem, unsigned long long& done) {
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess) done = true;
+    // the attribute belongs to the function on the current device: one bit
+    // of `done` per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) done |= bit;
     return e;
 }
 
@@ -22,7 +28,7 @@ int red_face_pq(const frk::Red<FR_REAL>& rd, const FR_REAL* u, const FR_REAL* uf
     auto k = frk::k_red_face<FR_DIM, P, Q, FR_REAL>;
     constexpr size_t sm = frk::smem_red<FR_DIM, P, Q, FR_REAL>(true);
     constexpr int W = frk::red_w<FR_DIM, P, Q, FR_REAL>(true);
-    static bool done = false;
+    static unsigned long long done = 0;
     const cudaError_t e = red_prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (rd.n <= 0) return 0;
@@ -37,7 +43,7 @@ int red_resid_pq(const frk::Red<FR_REAL>& rd, const FR_REAL* u, const FR_REAL* u
     auto k = frk::k_red_resid<FR_DIM, P, Q, FR_REAL, V>;
     constexpr size_t sm = frk::smem_red<FR_DIM, P, Q, FR_REAL>(false);
     constexpr int W = frk::red_w<FR_DIM, P, Q, FR_REAL>(false);
-    static bool done = false;
+    static unsigned long long done = 0;
     const cudaError_t e = red_prep(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (rd.n <= 0) return 0;

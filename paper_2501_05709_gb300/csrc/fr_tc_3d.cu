@@ -10,11 +10,17 @@ namespace frl {
 namespace {
 
 template <typename K>
-cudaError_t prep_tc(K kernel, size_t smem, bool& done) {
+cudaError_t prep_tc(K kernel, size_t smem, unsigned long long& done) {
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess) done = true;
+    // the attribute belongs to the function on the current device: one bit
+    // of `done` per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) done |= bit;
     return e;
 }
 
@@ -24,7 +30,7 @@ int resid_tc_p(const float* u, const float* uf, const float* fvn, int64_t E, con
                cudaStream_t s) {
     auto k = frk::k_residual<3, P, float, MP, VISC, BND, OPM>;
     const size_t sm = frk::smem_resid<3, P, float>(lc.epb, g.sS_sp != 0);
-    static bool done = false;
+    static unsigned long long done = 0;
     cudaError_t e = prep_tc(k, sm, done);
     if (e != cudaSuccess) return int(e);
     if (E == 0) return 0;

@@ -132,6 +132,28 @@ def test_graph_replay_with_orders_matches_direct():
         assert np.array_equal(F.fr_state_get(a), F.fr_state_get(b))
 
 
+def test_serial_and_forked_reduced_kernels_agree():
+    # a step runs the reduced-degree kernels on their own streams beside the
+    # degree-p kernels; the instrumented step (fr_profile_step) runs every
+    # kernel on one stream, one after the other: both write disjoint elements,
+    # so the states agree bit for bit
+    from paper_2501_05709_gb300 import fr as F
+    c = make_case("ns3d_walls_p2")
+    E = len(c["conn"])
+    caps = _caps(E, c["p"], seed=5)
+    m, _ = _oracle(c, None)
+    u = c["state"](m.xsp)
+    with F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c)) as a, \
+            F.fr_mesh_load((c["nodes"], c["conn"]), gpu_options(c)) as b:
+        for ctx in (a, b):
+            F.fr_set_element_order(ctx, caps)
+            F.fr_state_set(ctx, u)
+        F.fr_rk_step_graph(a, 3)
+        ms, n = F.fr_profile_step(b, 3)
+        assert n[5] > 0 and n[2] > 0
+        assert np.array_equal(F.fr_state_get(a), F.fr_state_get(b))
+
+
 def test_orders_on_one_candidate_and_removal():
     from paper_2501_05709_gb300 import fr as F
     c = make_case("ns3d_walls_p2")
