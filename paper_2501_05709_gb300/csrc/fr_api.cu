@@ -512,11 +512,9 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
         Real* uf_out = trace_buf(stage);
         int rc;
         if (c->visc) {
+            // the reduced-degree kernels first: their few, latency-bound
+            // blocks then start beside the degree-p kernel's
             if (fork) CK(fork_red(c, s));
-            if (pr) pr->mark_begin(1);
-            rc = L_visc<Real>(c, in, uf_in, s);
-            if (pr) pr->mark_end();
-            CKL(rc, "viscous face kernel");
             for (int q = 0; q < c->p; ++q)
                 if (c->red_n[q] > 0) {
                     if (pr) pr->mark_begin(5);
@@ -524,6 +522,10 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
                     if (pr) pr->mark_end();
                     CKL(rc, "reduced-degree face kernel");
                 }
+            if (pr) pr->mark_begin(1);
+            rc = L_visc<Real>(c, in, uf_in, s);
+            if (pr) pr->mark_end();
+            CKL(rc, "viscous face kernel");
             if (fork) CK(join_red(c, s));
         }
         if (stage == 1) {
@@ -562,10 +564,6 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
             cfac = c->ls_time[stage - 1];
         }
         if (fork) CK(fork_red(c, s));
-        if (pr) pr->mark_begin(2);
-        rc = L_resid<Real>(c, in, uf_in, st, s);
-        if (pr) pr->mark_end();
-        CKL(rc, "residual kernel");
         for (int q = 0; q < c->p; ++q)
             if (c->red_n[q] > 0) {
                 if (pr) pr->mark_begin(5);
@@ -573,6 +571,10 @@ int enqueue_step(fr_ctx* c, cudaStream_t s, Prof* pr = nullptr) {
                 if (pr) pr->mark_end();
                 CKL(rc, "reduced-degree residual kernel");
             }
+        if (pr) pr->mark_begin(2);
+        rc = L_resid<Real>(c, in, uf_in, st, s);
+        if (pr) pr->mark_end();
+        CKL(rc, "residual kernel");
         if (fork) CK(join_red(c, s));
         if (c->src_nentry > 0) {
             if (pr) pr->mark_begin(4);
@@ -624,9 +626,22 @@ int enqueue_residual(fr_ctx* c, const Real* u, Real* R, cudaStream_t s) {
     return FR_OK;
 }
 
+// FP64 -> FP32 over n values; two values per 16-byte load when both arrays
+// are aligned for it (the source may be host memory read over the CPU-GPU
+// link, where wider requests move more bytes per request)
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        b[i] = float(a[i]);
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, st = int64_t(gridDim.x) * blockDim.x;
+    if ((reinterpret_cast<uintptr_t>(a) & 15) == 0 && (reinterpret_cast<uintptr_t>(b) & 7) == 0) {
+        const double2* a2 = reinterpret_cast<const double2*>(a);
+        float2* b2 = reinterpret_cast<float2*>(b);
+        for (int64_t i = t0; i < n / 2; i += st) {
+            const double2 x = a2[i];
+            b2[i] = make_float2(float(x.x), float(x.y));
+        }
+        if (t0 == 0 && (n & 1)) b[n - 1] = float(a[n - 1]);
+    } else {
+        for (int64_t i = t0; i < n; i += st) b[i] = float(a[i]);
+    }
 }
 __global__ void k_f2d(const float* a, double* b, int64_t n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
