@@ -627,6 +627,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwh", action="store_true", help="skip the FW-H/PSD post-processing timing")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="skip the p=4 leg (FP32, TF32 and BF16x3 tensor-core modes) of the default run")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 12-candidate leg (timed after the headline workload)")
     ap.add_argument("--tile", type=int, default=0, help="elements per block (0: autotune)")
@@ -679,6 +681,21 @@ def main():
                    "note": "the FW-H window at an observer 10c away needs ~0.6 convective times, far more than "
                            "these steps cover; OASPL mixed vs FP64 per candidate comes from the batched precision "
                            "study (cases.py batch-precision)"}
+    # config 4: the TGV box at p=4 in FP32 (with its FP64 counterpart) and in
+    # the two tensor-core line-operator modes
+    config4 = None
+    if not args.no_config4 and args.workload == "tgv32_p3" and args.precision == "fp32":
+        config4 = {"workload": "tgv32_p4", "description": WORKLOADS["tgv32_p4"], "steps": args.steps,
+                   "warmup": args.warmup, "modes": {}}
+        for mode in ("fp32", "tf32", "bf16x3"):
+            m4 = argparse.Namespace(**vars(args))
+            m4.workload, m4.precision, m4.sponge, m4.tile = "tgv32_p4", mode, False, 0
+            m4.no_fp64 = args.no_fp64 or mode != "fp32"
+            r4 = gpu_leg(m4, rank, world, local_rank)
+            config4["modes"][mode] = {
+                "value": r4["value"], "unit": UNIT, "ms_per_step": r4["ms"] / args.steps,
+                "dtype": {"fp32": "f32", "tf32": "f32+tf32-tc", "bf16x3": "f32+bf16x3-tc"}[mode],
+                "roofline": r4["roofline"], "kernels": r4["kernels"], "clocks": r4["clocks"], "fp64": r4["fp64"]}
     fwh = None
     if rank == 0 and not args.no_fwh:
         try:
@@ -707,7 +724,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "f32+tf32-tc", "bf16x3": "f32+bf16x3-tc", "fp64": "f64"}[args.precision],
                 "data": "synthetic", "config": config, "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
                 "clocks": r["clocks"], "kernels": r["kernels"], "fp64": r["fp64"], "cpu_baseline_all_cores": cb_all,
-                "batched": batched, "fwh": fwh}
+                "batched": batched, "config4": config4, "fwh": fwh}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch
