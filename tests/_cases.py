@@ -165,7 +165,8 @@ def coef_floor(solver, u, pick=None, draws=2, seed=1):
     """Relative L2 change of the oracle residual when every operator
     coefficient (D, extrapolation and correction weights) and every metric
     value (S, |J|, normals) moves by one unit in the last place: the floor set
-    by how the data of the discretisation itself is rounded."""
+    by how the data of the discretisation itself is rounded.  The solver's
+    energy sources and per-element degrees are kept."""
     import copy
 
     from oracle.fr import FRSolver
@@ -186,7 +187,7 @@ def coef_floor(solver, u, pick=None, draws=2, seed=1):
         m2.ref = r2
         for name in ("S", "J", "N"):
             setattr(m2, name, jig(getattr(m2, name)))
-        R2 = FRSolver(m2, solver.ph).residual(u)
+        R2 = FRSolver(m2, solver.ph, source=solver.source, caps=solver.caps).residual(u)
         if pick is not None:
             R2 = R2[pick]
         worst = max(worst, float(np.linalg.norm((R2 - ref).ravel()) / np.linalg.norm(ref.ravel())))

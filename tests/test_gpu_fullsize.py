@@ -3,6 +3,7 @@ quadratic hexahedra p=3), in the bench's launch configuration (autotuned
 tiles): sampled elements against the oracle, plus properties that hold at any
 size (discrete conservation), plus the batched multi-candidate context."""
 import math
+import types
 
 import numpy as np
 import pytest
@@ -165,6 +166,51 @@ def test_naca100k_sampled_residual(precision, tol):
         m, s = make(sn, sc)
         tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids], solver=s, pick=pos)
     assert _rel(R[ids], Ro) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-4)])
+def test_naca100k_sponge_sampled_residual(precision, tol):
+    # the NACA O-grid with its far-field sponge (degree 3 inside 4c, then 2,
+    # 1, 0 past 4c, 6c, 8c): sampled elements of every degree, and degree-3
+    # elements beside reduced ones, against the oracle's degree-q elements
+    from oracle.fr import FRSolver
+    from oracle.mesh import Mesh
+    from oracle.physics import NavierStokes
+    from oracle.sponge import project
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    from ._subset import submesh
+    nodes, conn = _naca100k()
+    caps = W.sponge_orders(nodes, 3)
+    rho, vel, p = W.freestream(0.2, 3.0)
+    opts = F.options(order=3, precision=precision, viscous=True, mu=1 / 23000, rho_inf=rho, p_inf=p,
+                     vel_inf=tuple(vel), dt=1e-5)
+    E = len(nodes)
+    u = W.perturbed_uniform(E, 64, rho, vel, p, amplitude=0.01, seed=1)
+    # the state of a reduced element lies in its degree-q space
+    u = project(types.SimpleNamespace(p=3, dim=3), u, caps)
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        F.fr_set_element_order(ctx, caps)
+        F.fr_autotune(ctx)
+        dt = torch.float64 if precision == 0 else torch.float32
+        ud = torch.tensor(u, dtype=dt, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+    rng = np.random.default_rng(3)
+    sample = [int(rng.choice(np.nonzero(caps == q)[0])) for q in range(4) for _ in range(3)]
+    # degree-3 elements with a reduced neighbour
+    border = [e for e in np.nonzero(caps == 3)[0] if any(c >= 0 and caps[c] < 3 for c in conn[e, :, 0])]
+    sample += [int(b) for b in rng.choice(border, 3, replace=False)]
+    sample = np.unique(np.array(sample, np.int64))
+    sn, sc, sids, pos = submesh(nodes, conn, sample)
+    ph = NavierStokes(3, mu=1 / 23000, freestream=(rho, vel, p))
+    s = FRSolver(Mesh(sn, sc, 3), ph, caps=caps[sids])
+    Ro = s.residual(u[sids])[pos]
+    if precision == 0:
+        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids], solver=s, pick=pos)
+    assert _rel(R[sample], Ro) <= tol
 
 
 def test_batched_candidates_match_separate_runs():
