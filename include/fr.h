@@ -145,7 +145,12 @@ int fr_cand_range(const fr_ctx* ctx, int cand, int64_t* first, int64_t* count);
  * non-finite flags (fr_nonfinite).  fr_state_get copies the state and then
  * returns FR_ENONFINITE when an addressed candidate's flag is set (or, for a
  * host copy, when a copied value is NaN or Inf).  Both calls synchronise the
- * given stream before returning. */
+ * given stream before returning.  A host array that the CUDA runtime has
+ * page-locked and mapped (cudaHostAlloc, cudaHostRegister, a pinned torch
+ * tensor) is read or written in place by the conversion kernel over the
+ * CPU-GPU link; pageable host memory goes through a device staging buffer
+ * (allocated on first use, E * nvar * Nsp doubles, FR_ENOMEM if that fails).
+ * Both give the same state bit for bit. */
 int fr_state_set(fr_ctx* ctx, int cand, const double* u, int on_device, void* stream);
 int fr_state_get(fr_ctx* ctx, int cand, double* u, int on_device, void* stream);
 
