@@ -213,6 +213,48 @@ def test_naca100k_sponge_sampled_residual(precision, tol):
     assert _rel(R[sample], Ro) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-4)])
+def test_batch12_sampled_residual(precision, tol):
+    # config 5 at its full size: the twelve uneven O-grids of the MADS poll
+    # (599,888 curved hexes) in one context with autotuned tiles; sampled
+    # elements (wall ring, mid-field, far field) of three candidates against
+    # the oracle on each candidate's sub-mesh
+    from oracle.fr import FRSolver
+    from oracle.mesh import Mesh
+    from oracle.physics import NavierStokes
+    from paper_2501_05709_gb300 import cases as C
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    from ._subset import submesh
+    params = C.batch_params(12, seed=1)
+    meshes = [C.naca_setup(naca=prm["naca"], n_theta=prm["n_theta"], n_r=prm["n_r"])[:2] for prm in params]
+    opts, (rho, vel, p) = C.naca_options(precision=precision)
+    states = [W.perturbed_uniform(len(n), 64, rho, vel, p, amplitude=0.01, seed=k)
+              for k, (n, _) in enumerate(meshes)]
+    with F.fr_mesh_load(meshes, opts) as ctx:
+        F.fr_autotune(ctx)
+        offs = [F.fr_cand_range(ctx, k)[0] for k in range(len(meshes))]
+        dt = torch.float64 if precision == 0 else torch.float32
+        ud = torch.tensor(np.concatenate(states), dtype=dt, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+        del ud, Rd
+    ph = NavierStokes(3, mu=rho / 23000.0, freestream=(rho, vel, p))
+    for k in (0, 5, 11):
+        nodes, conn = meshes[k]
+        nt = params[k]["n_theta"]
+        sample = np.array([0, nt - 1, 3 * nt + 5, len(nodes) // 2, len(nodes) - nt // 2, len(nodes) - 1])
+        sn, sc, sids, pos = submesh(nodes, conn, sample)
+        s = FRSolver(Mesh(sn, sc, 3), ph)
+        Ro = s.residual(states[k][sids])[pos]
+        bar = tol
+        if precision == 0:
+            bar = fp64_tol(lambda v: s.residual(v)[pos], states[k][sids], solver=s, pick=pos)
+        assert _rel(R[offs[k] + np.unique(sample)], Ro) <= bar, k
+
+
 def test_batched_candidates_match_separate_runs():
     from paper_2501_05709_gb300 import fr as F
     from paper_2501_05709_gb300 import workloads as W
