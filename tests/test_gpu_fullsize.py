@@ -97,6 +97,38 @@ def test_tgv32_sampled_residual(state, precision, tol):
     assert _rel(R[ids], Ro) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [(0, None), (1, 1e-4)])
+def test_tgv32_p4_sampled_residual(precision, tol):
+    # config 4's mesh at p=4 (125 points per element, two warps per element)
+    # on a smooth state, in the bench's launch configuration; FP32 under the
+    # bound stated for the FP32 mode on the O-grids (1e-4)
+    from oracle.physics import NavierStokes
+    from paper_2501_05709_gb300 import fr as F
+    from paper_2501_05709_gb300 import workloads as W
+    from ._subset import submesh
+    nodes, conn = _tgv()
+    opts = F.options(order=4, precision=precision, viscous=True, mu=1 / 1600, p_inf=1 / (1.4 * 0.01), dt=1.5e-4)
+    with F.fr_mesh_load((nodes, conn), opts) as ctx:
+        xsp = F.fr_sp_coords(ctx)
+        u = np.ascontiguousarray(np.moveaxis(W.random_smooth_state(xsp, seed=6, periods=[2 * math.pi] * 3), 0, 1))
+        F.fr_autotune(ctx)
+        dt = torch.float64 if precision == 0 else torch.float32
+        ud = torch.tensor(u, dtype=dt, device="cuda")
+        Rd = torch.empty_like(ud)
+        F.fr_residual(ctx, ud, Rd)
+        torch.cuda.synchronize()
+        R = Rd.double().cpu().numpy()
+    rng = np.random.default_rng(12)
+    sample = np.unique(np.concatenate([[0, 31, 1023, 32767], rng.choice(32768, 12, replace=False)]))
+    make = _solver(NavierStokes(3, mu=1 / 1600), p=4)
+    sn, sc, sids, pos = submesh(nodes, conn, sample)
+    m, s = make(sn, sc)
+    Ro = s.residual(u[sids])[pos]
+    if precision == 0:
+        tol = fp64_tol(lambda v: s.residual(v)[pos], u[sids], solver=s, pick=pos)
+    assert _rel(R[sample], Ro) <= tol
+
+
 def test_tgv32_fp32_state_tracks_fp64():
     # the FP32 state after 40 RK4 steps stays within 2e-6 (relative L2) of FP64
     from paper_2501_05709_gb300 import fr as F
