@@ -54,6 +54,30 @@ __device__ __forceinline__ void grp_sync(int grp) {
     }
 }
 
+// Face point (side, fp) of the two faces normal to one direction that thread
+// `lane` of an element group handles at iteration it; false when it has none.
+// One warp per element: t = lane + 32 it runs over side 0, then side 1.  Two
+// warps (p = 4 in 3D, 25 points per face, one iteration): the first warp takes
+// the 25 points of side 0 and points 0-2 of side 1, the second warp points
+// 3-24 of side 1.  The two faces' [v][fp] rows lie 125 floats (29 banks) apart,
+// so side-1 points 0-2 use banks 29-31, which side 0 leaves free; points 0-6
+// (the plain split) would put two words on each of banks 0-3.
+template <int DIM, int P>
+__device__ __forceinline__ bool face_pt(int lane, int it, int& side, int& fp) {
+    constexpr int T = Grp<DIM, P>::T, NFP = Sz<DIM, P>::NFP;
+    if constexpr (T == 64) {
+        static_assert(NFP == 25 && Sz<DIM, P>::NV == 5, "the two-warp face split is laid out for p = 4 in 3D");
+        side = lane < NFP ? 0 : 1;
+        fp = lane < NFP ? lane : lane < 32 ? lane - NFP : lane - 29;
+        return lane < 28 || (lane >= 32 && lane < 54);
+    } else {
+        const int t = lane + T * it;
+        side = t >= NFP ? 1 : 0;
+        fp = t - side * NFP;
+        return t < 2 * NFP;
+    }
+}
+
 // solution point j (along direction d) of the line through face point fp of a
 // face normal to d; face points enumerate the remaining directions in
 // increasing order, the lower one fastest
@@ -924,10 +948,8 @@ __device__ __forceinline__ void visc_faces_affine(const Real* su, const Real* sl
         for (int d = 0; d < DIM; ++d) {
 #pragma unroll
             for (int it = 0; it < NFI; ++it) {
-                const int t = lane + T * it;
-                if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
-                const int side = t >= NFP ? 1 : 0;
-                const int fp = t - side * NFP;
+                int side, fp;
+                if (!face_pt<DIM, P>(lane, it, side, fp)) continue;
                 const int f = 2 * d + side;
                 const int code = side ? codes[2 * d + 1] : codes[2 * d];  // static register indices
                 const Real* N = sgeo + DIM * DIM + 1 + f * DIM;
@@ -1191,10 +1213,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + T * it;
-            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
-            const int side = t >= NFP ? 1 : 0;
-            const int fp = t - side * NFP;
+            int side, fp;
+            if (!face_pt<DIM, P>(lane, it, side, fp)) continue;
             const int f = 2 * d + side;
             Real uL[NV], uc[NV];
 #pragma unroll
@@ -1280,9 +1300,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + T * it;
-            const int side = t >= NFP ? 1 : 0;
-            if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
+            int side, fp;
+            if (face_pt<DIM, P>(lane, it, side, fp)) load_normal<DIM>(g, e, 2 * d + side, fp, Nr[d][it]);
         }
     grp_sync<T>(warp);
     // D: lifted face gradient, viscous normal flux
@@ -1290,10 +1309,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 80 : 168) k_visc_face(const Real
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + T * it;
-            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
-            const int side = t >= NFP ? 1 : 0;
-            const int fp = t - side * NFP;
+            int side, fp;
+            if (!face_pt<DIM, P>(lane, it, side, fp)) continue;
             const int f = 2 * d + side;
             const Real nsg = side ? Real(1) : Real(-1);
             Real cf[NP];
@@ -1411,9 +1428,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + T * it;
-            const int side = t >= NFP ? 1 : 0;
-            if (t < 2 * NFP) load_normal<DIM>(g, e, 2 * d + side, t - side * NFP, Nr[d][it]);
+            int side, fp;
+            if (face_pt<DIM, P>(lane, it, side, fp)) load_normal<DIM>(g, e, 2 * d + side, fp, Nr[d][it]);
         }
     Real pu0[NSPW][NV], pacc[NSPW][NV];
     if constexpr (PREFETCH) {
@@ -1437,10 +1453,8 @@ __global__ void __maxnreg__(sizeof(Real) == 4 ? 96 : 168) k_residual(const Real*
     for (int d = 0; d < DIM; ++d) {
 #pragma unroll
         for (int it = 0; it < NFI; ++it) {
-            const int t = lane + T * it;
-            if ((2 * NFP) % T != 0 && t >= 2 * NFP) break;
-            const int side = t >= NFP ? 1 : 0;
-            const int fp = t - side * NFP;
+            int side, fp;
+            if (!face_pt<DIM, P>(lane, it, side, fp)) continue;
             const int f = 2 * d + side;
             Real uL[NV], uR[NV], uc[NV];
 #pragma unroll

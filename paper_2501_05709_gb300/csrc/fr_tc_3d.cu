@@ -20,6 +20,12 @@ cudaError_t prep_tc(K kernel, size_t smem, unsigned long long& done) {
     const unsigned long long bit = 1ull << (dev & 63);
     if (done & bit) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // and to the largest shared-memory carveout: left to itself the driver
+    // configured too little shared memory for the blocks that the registers
+    // admit (four blocks per SM at p = 4 in 3D where five or six fit)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
     if (e == cudaSuccess) done |= bit;
     return e;
 }
