@@ -107,15 +107,23 @@ def make_case(name):
         c["nodes"], c["conn"] = W.box_mesh(3, [3, 2, 2], 0.0, 1.0, q=2, curve=0.1, seed=9)
         c.update(p=4, kind=1, mu=0.02, visc=True)
         c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=8)
-    elif name in ("turned3d_curved_p3", "turned3d_affine_p3", "turned2d_curved_p2_g2"):
+    elif name in ("turned3d_curved_p3", "turned3d_affine_p3", "turned2d_curved_p2_g2", "turned3d_affine_p4",
+                  "turned3d_curved_p4"):
         # every element's local frame turned by a seeded rotation of the
-        # reference element: faces carry all orientation codes
+        # reference element: faces carry all orientation codes (at p = 4 the
+        # face phases run on two warps per element)
         if name == "turned3d_curved_p3":
             nodes, conn = W.box_mesh(3, 3, 0.0, 1.0, q=2, curve=0.1, seed=3)
             c.update(p=3, mu=0.02, visc=True)
         elif name == "turned3d_affine_p3":
             nodes, conn = W.box_mesh(3, [4, 3, 3], 0.0, 1.0, q=1)
             c.update(p=3, mu=0.02, visc=True)
+        elif name == "turned3d_affine_p4":
+            nodes, conn = W.box_mesh(3, [3, 3, 2], 0.0, 1.0, q=1)
+            c.update(p=4, mu=0.02, visc=True)
+        elif name == "turned3d_curved_p4":
+            nodes, conn = W.box_mesh(3, [3, 2, 2], 0.0, 1.0, q=2, curve=0.1, seed=4)
+            c.update(p=4, mu=0.02, visc=True)
         else:
             nodes, conn = W.box_mesh(2, [4, 3], 0.0, 1.0, q=2, curve=0.1, seed=2)
             c.update(p=2, kind=1, mu=0.01, visc=True)
@@ -145,7 +153,8 @@ def make_case(name):
 CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d_walls_p2", "ns3d_ogrid_p3",
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
          "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2", "turned3d_curved_p3", "turned3d_affine_p3",
-         "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2", "tgv3d_p4", "rot3d_p4"]
+         "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2", "tgv3d_p4", "rot3d_p4",
+         "turned3d_affine_p4", "turned3d_curved_p4"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):
