@@ -50,12 +50,16 @@ def make_case(name):
         c["nodes"], c["conn"] = W.box_mesh(3, [3, 4, 2], 0.0, [1.5, 1.0, 0.5], q=2, walls_y=True, curve=0.05)
         c.update(p=2, mu=0.02, visc=True)
         c["state"] = lambda x: _conserved_at(x, W.random_smooth_state, seed=6, periods=[1.5, 1.0, 0.5])
-    elif name in ("ns3d_ogrid_p3", "euler3d_ogrid_p2"):
+    elif name in ("ns3d_ogrid_p3", "euler3d_ogrid_p2", "ns3d_ogrid_p4"):
+        # curved O-grid with a no-slip body and a characteristic far field (at
+        # p = 4 the boundary kernels on two warps per element)
         c["nodes"], c["conn"] = W.ogrid_mesh(12, 3, 2, 0.2, r_outer=3.0, first_cell=0.05)
         rho, vel, p = W.freestream(0.2, 3.0)
         c["freestream"] = (rho, vel, p)
         if name == "ns3d_ogrid_p3":
             c.update(p=3, mu=1.0 / 2300.0, visc=True, dt=2e-4)
+        elif name == "ns3d_ogrid_p4":
+            c.update(p=4, mu=1.0 / 2300.0, visc=True, dt=1e-4)
         else:
             c.update(p=2, dt=2e-4)
         nsp = (c["p"] + 1) ** 3
@@ -74,17 +78,17 @@ def make_case(name):
         else:
             c.update(p=2)
         c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=10)
-    elif name in ("walls3d_p2", "rotwalls3d_p3"):
+    elif name in ("walls3d_p2", "rotwalls3d_p3", "rotwalls3d_p4"):
         # straight-sided channel with no-slip walls on both y faces: axis-aligned
-        # (walls3d_p2) or turned about (1, 2, 3) (rotwalls3d_p3)
+        # (walls3d_p2) or turned about (1, 2, 3) (rotwalls3d_p3, rotwalls3d_p4)
         nodes, c["conn"] = W.box_mesh(3, [3, 4, 2], 0.0, [1.5, 1.0, 0.5], q=1, walls_y=True)
         R = np.eye(3)
-        if name == "rotwalls3d_p3":
+        if name != "walls3d_p2":
             ax = np.array([1.0, 2.0, 3.0]) / math.sqrt(14.0)
             K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
             R = np.eye(3) + math.sin(0.5) * K + (1 - math.cos(0.5)) * K @ K
         c["nodes"] = np.ascontiguousarray(np.asarray(nodes) @ R.T)
-        c.update(p=2 if name == "walls3d_p2" else 3, mu=0.02, visc=True)
+        c.update(p={"walls3d_p2": 2, "rotwalls3d_p3": 3, "rotwalls3d_p4": 4}[name], mu=0.02, visc=True)
         c["state"] = lambda x: _conserved_at(np.asarray(x) @ R, W.random_smooth_state, seed=11,
                                              periods=[1.5, 1.0, 0.5])
     elif name == "farfield3d_euler_p2":
@@ -154,7 +158,7 @@ CASES = ["vortex2d_p2", "ns2d_curved_p3_g2", "tgv3d_p3", "ns3d_curved_p3", "ns3d
          "euler3d_ogrid_p2", "ns3d_p1", "ns3d_p4_g2", "single_element", "rot3d_p3", "walls3d_p2", "rotwalls3d_p3",
          "farfield3d_euler_p2", "walls2d_p3", "rot3d_euler_p2", "turned3d_curved_p3", "turned3d_affine_p3",
          "turned2d_curved_p2_g2", "turned_ogrid_p3", "turned_ogrid_euler_p2", "tgv3d_p4", "rot3d_p4",
-         "turned3d_affine_p4", "turned3d_curved_p4"]
+         "turned3d_affine_p4", "turned3d_curved_p4", "rotwalls3d_p4", "ns3d_ogrid_p4"]
 
 
 def ulp_floor(fn, u, draws=2, seed=0):

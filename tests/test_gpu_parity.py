@@ -45,7 +45,8 @@ def test_residual_fp64(name):
 
 METRIC_PATH = {"vortex2d_p2": 2, "tgv3d_p3": 2, "single_element": 2, "rot3d_p3": 1, "walls3d_p2": 2,
                "rotwalls3d_p3": 1, "farfield3d_euler_p2": 2, "walls2d_p3": 2, "rot3d_euler_p2": 1,
-               "turned3d_affine_p3": 1, "tgv3d_p4": 2, "rot3d_p4": 1, "turned3d_affine_p4": 1}
+               "turned3d_affine_p3": 1, "tgv3d_p4": 2, "rot3d_p4": 1, "turned3d_affine_p4": 1,
+               "rotwalls3d_p4": 1}
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -61,7 +62,7 @@ def test_affine_detection(name):
 @pytest.mark.parametrize("name", ["vortex2d_p2", "tgv3d_p3", "ns3d_ogrid_p3", "ns3d_walls_p2", "rot3d_p3",
                                   "rotwalls3d_p3", "farfield3d_euler_p2", "turned3d_curved_p3", "turned_ogrid_p3",
                                   "turned2d_curved_p2_g2", "tgv3d_p4", "rot3d_p4", "turned3d_affine_p4",
-                                  "turned3d_curved_p4"])
+                                  "turned3d_curved_p4", "rotwalls3d_p4", "ns3d_ogrid_p4"])
 def test_rk4_steps_fp64(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
@@ -116,7 +117,7 @@ def test_conservation_on_gpu(name):
     assert np.all(np.abs(after[:nv] - before[:nv]) <= 1e-12 * scale)
 
 
-@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3"])
+@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3", "ns3d_ogrid_p4"])
 def test_forces_match_oracle(name):
     from paper_2501_05709_gb300 import fr as F
     c = make_case(name)
@@ -141,7 +142,7 @@ def test_forces_match_oracle(name):
     assert out[4] == 1.0
 
 
-@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3"])
+@pytest.mark.parametrize("name", ["ns3d_ogrid_p3", "turned_ogrid_p3", "ns3d_ogrid_p4"])
 def test_sampling_matches_oracle(name):
     from oracle.sampling import locate, sample
     from paper_2501_05709_gb300 import fr as F
